@@ -1,0 +1,322 @@
+"""Benchmark of the BST filtered-backprojection path on GB300.
+
+One step = BST FBP of the whole workload volume (default: 2048 slices x 2048
+angles x 2048 rays FP32 -> 2048^3 FP32 volume, pad factor 2), with inputs
+resident in HBM.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): every rank reconstructs its own
+volume of the same size (weak scaling, no collective on the data path); the
+timed region is bracketed by barriers and the slowest rank's time is used.
+
+--impl reference times the FP64 CPU oracle (the plain restatement of the
+method used by the tests) on the host cores, on a bounded sample of the same
+workload (one slice per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "BST FBP voxels/s and % HBM roofline at 2048³ FP32 on 1 GB300 vs brute-force BP"
+UNIT = "voxels/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+# FP32 ALU peak of GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fft_flops(M: int) -> float:
+    return 5.0 * M * np.log2(M)
+
+
+def disk_points(M: int) -> int:
+    k = np.arange(M) - M // 2
+    return int(np.count_nonzero(k[None, :] ** 2 + k[:, None] ** 2 < (M // 2) ** 2))
+
+
+def stage_flops(N: int, V: int, M: int) -> dict:
+    """Algorithmic flops per launch (one slice pair) of each kernel of the
+    forward path: conventional 5 M log2 M per complex FFT line, 6 flops per
+    weighted spectrum sample, 12 per bilinear gather (three complex lerps),
+    2 per kept output sample."""
+    return {
+        0: V * (fft_flops(M) + 6.0 * M),
+        1: M * fft_flops(M) + 12.0 * disk_points(M),
+        2: N * fft_flops(M) + 2.0 * N * N * 2,
+    }
+
+
+STAGE_NAMES = {0: "k_ray_fft", 1: "k_grid_col", 2: "k_row_ifft", 3: "k_ss_filter", 4: "k_ss_bp"}
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if len(s) > 3 + i and s[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def oracle_slice_time(N: int, V: int, slices: int = 1):
+    """Time the FP64 oracle (BST FBP) on `slices` host-generated slices."""
+    import synth
+    from oracle import bst as ob
+    theta, sino, _ = synth.workload_slices("volume-2048", list(range(slices)), rays=N, angles=V)
+    t0 = time.perf_counter()
+    for s in range(slices):
+        ob.fbp(sino[s].astype(np.float64), theta)
+    return time.perf_counter() - t0
+
+
+def run_reference(args, rank, world):
+    N = V = args.rays
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_slice_time(N, V, 1)
+    times = [oracle_slice_time(N, V, 1) for _ in range(args.steps)]
+    per_step = float(np.mean(times))
+    value = N * N / per_step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "volume-2048 (2048 slices x 2048 angles x 2048 rays FP32, pad 2)",
+                   "step": "one slice of the workload through the FP64 numpy oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "1 slice (2048 x 2048) per step, FP64 numpy oracle, single-threaded"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1704_08364_gb300 as bst
+    from paper_1704_08364_gb300 import _lib
+    import synth
+    from synth import device as sdev
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    N = V = args.rays
+    S = args.slices
+    alpha = args.pad
+    theta = synth.uniform_angles(V)
+    plan = bst.Plan(N, theta, alpha)
+    M = plan.M
+    sino = sdev.ellipse_volume(synth.WORKLOADS["volume-2048"].index, S, V, N, noise_frac=0.01, device=dev)
+    vol = torch.empty((S, N, N), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        plan.fbp(sino, out=vol)
+    plan.status()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(args.steps):
+            plan.fbp(sino, out=vol)
+        e1.record(st)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    plan.status()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * S * N * N / (ms / 1e3)
+
+    # per-kernel device times over K more steps (events after every launch)
+    L = _lib.load()
+    import ctypes
+    L.bst_plan_set_timing(plan.handle, 1)
+    for _ in range(args.steps):
+        plan.fbp(sino, out=vol)
+    sms = (ctypes.c_double * 8)()
+    sl = (ctypes.c_longlong * 8)()
+    L.bst_plan_timing(plan.handle, sms, sl, 8)
+    L.bst_plan_set_timing(plan.handle, 0)
+    stage_ms = {s: sms[s] for s in range(3)}
+    stage_n = {s: sl[s] for s in range(3)}
+    flops = stage_flops(N, V, M)
+    dom = max(stage_ms, key=lambda s: stage_ms[s])
+    avg_ms = stage_ms[dom] / max(stage_n[dom], 1)
+    hbm_peak, sm_max, src = _peaks()
+    peak_tf = fp32_peak_tflops(sm_max)
+    achieved_tf = flops[dom] / (avg_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": STAGE_NAMES[dom], "achieved": achieved_tf, "peak": peak_tf,
+                "unit": "TFLOP/s", "frac": achieved_tf / peak_tf, "traffic": None,
+                "peak_source": "FP32 152 SM x 128 lanes x 2 x %.0f MHz (derived)" % sm_max,
+                "stage_share": {STAGE_NAMES[s]: stage_ms[s] / max(sum(stage_ms.values()), 1e-9) for s in stage_ms},
+                "stage_avg_us": {STAGE_NAMES[s]: 1e3 * stage_ms[s] / max(stage_n[s], 1) for s in stage_ms}}
+    alg_bytes = 4.0 * (V * N + N * N) * S
+    path_hbm = {"algorithmic_bytes_per_step": alg_bytes, "achieved_gbs": alg_bytes / (ms / 1e3) / 1e9,
+                "peak_gbs": hbm_peak, "frac": alg_bytes / (ms / 1e3) / 1e9 / hbm_peak, "peak_source": src}
+
+    # brute-force slant stack on a slice subset, extrapolated per slice
+    bs = min(args.brute_slices, S)
+    out_b = torch.empty((bs, N, N), dtype=torch.float32, device=dev)
+    plan.brute_backproject(sino[:bs], out=out_b)
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(st)
+    plan.brute_backproject(sino[:bs], out=out_b)
+    b1.record(st)
+    torch.cuda.synchronize()
+    brute_ms_per_slice = b0.elapsed_time(b1) / bs
+    bst_ms_per_slice = ms / S
+
+    # end to end: pinned host input -> device -> FBP -> pinned host output
+    e2e = None
+    es = min(args.e2e_slices, S)
+    try:
+        h_in = torch.empty((es, V, N), dtype=torch.float32, pin_memory=True)
+        h_in.copy_(sino[:es])
+        h_out = torch.empty((es, N, N), dtype=torch.float32, pin_memory=True)
+        d_in = torch.empty((es, V, N), dtype=torch.float32, device=dev)
+        d_out = torch.empty((es, N, N), dtype=torch.float32, device=dev)
+        for _ in range(2):
+            d_in.copy_(h_in, non_blocking=True)
+            plan.fbp(d_in, out=d_out)
+            h_out.copy_(d_out, non_blocking=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            d_in.copy_(h_in, non_blocking=True)
+            plan.fbp(d_in, out=d_out)
+            h_out.copy_(d_out, non_blocking=True)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        e2e = {"value": world * es * N * N / dt, "unit": UNIT, "h2d_bytes_per_step": es * V * N * 4,
+               "d2h_bytes_per_step": es * N * N * 4, "slices": es}
+        del h_in, h_out, d_in, d_out
+    except Exception as ex:  # pragma: no cover - host memory limits
+        e2e = {"value": None, "unit": UNIT, "error": str(ex)[:200]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        ns = 2
+        t = oracle_slice_time(N, V, ns)
+        cpu = {"value": ns * N * N / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{ns} slices of {N}x{N} (same workload), FP64 numpy oracle BST FBP, single-threaded"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"volume-{N} ({S} slices x {V} angles x {N} rays FP32, pad {alpha}, M={M})",
+                       "slices_per_gpu": S, "l2": "inputs (%.1f GiB) larger than L2" % (S * V * N * 4 / 2**30),
+                       "parallelism": f"slices, {world} GPU(s), weak"},
+            "slices_per_s": world * S / (ms / 1e3),
+            "roofline": roofline, "path_hbm": path_hbm,
+            "vs_brute": {"brute_ms_per_slice": brute_ms_per_slice, "bst_ms_per_slice": bst_ms_per_slice,
+                         "speedup": brute_ms_per_slice / bst_ms_per_slice, "brute_slices_timed": bs},
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 3 * ((S + 1) // 2) * args.steps,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rays", type=int, default=2048)
+    ap.add_argument("--slices", type=int, default=2048)
+    ap.add_argument("--pad", type=int, default=2)
+    ap.add_argument("--brute-slices", type=int, default=64)
+    ap.add_argument("--e2e-slices", type=int, default=2048)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * bst.h -- C ABI of libbst: filtered backprojection of parallel-beam
+ * sinograms through the backprojection-slice theorem (BST) on one GPU.
+ *
+ * Method: Theorem 2.1 (Eq. 3) of "Low-complexity Distributed Tomographic
+ * Backprojection for large datasets": the 2D Fourier transform of the
+ * backprojection b = B y (Eq. 2) at the polar point sigma (cos t, sin t) is
+ * y^(sigma, t) / sigma.  Sec. 2 evaluates it in stages P0..P8: zero padding,
+ * a 1D FFT along the detector, a 1/sigma (or filter) weight, polar-to-
+ * Cartesian interpolation in the Fourier domain, a 2D inverse FFT and an
+ * fftshift/crop, O(N^2 log N) per slice instead of the O(N^3) slant stack.
+ *
+ * Conventions (the paper fixes none; these are this library's):
+ *   - N detector samples at t_i = (i - N/2) dt, dt = 2/N (t in [-1, 1));
+ *   - images are N x N with volume[r][c] at u = ((c - N/2) dt, (r - N/2) dt):
+ *     the column index follows u1, the row index u2; theta = 0 has t = u1;
+ *   - V angles theta_j (radians, float32), strictly increasing, in [0, pi);
+ *   - pad factor alpha in {1, 2}; FFT length M = alpha N; supported M are
+ *     2^a (16 <= M <= 4096) and 3 * 2^a (48 <= M <= 3072); N is even;
+ *   - sinogram[slices][V][N], volume[slices][N][N]: row-major, contiguous
+ *     float32, device memory owned by the caller; the library never frees or
+ *     retains caller pointers;
+ *   - the ordinary-frequency Fourier convention, so Eq. 3 holds with
+ *     constant 1; bilinear interpolation in (signed radius, angle); the
+ *     Nyquist bin is zero; the DC bin is averaged over angles.
+ *
+ * Every call is asynchronous on the given stream.  The returned status
+ * covers argument validation and launch errors only; errors detected on the
+ * device are sticky in the plan and reported by bst_plan_status().  Calls on
+ * one plan may be issued from one host thread at a time.
+ */
+#ifndef BST_H
+#define BST_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BST_OK = 0,
+    BST_ERR_INVALID_ARGUMENT = 1,   /* null pointer, bad count, bad angles, aliasing */
+    BST_ERR_UNSUPPORTED_SIZE = 2,   /* M = alpha N not a supported FFT length, N odd */
+    BST_ERR_WORKSPACE_TOO_SMALL = 3,
+    BST_ERR_CUDA = 4,               /* a CUDA runtime call or launch failed */
+    BST_ERR_TIMEOUT = 5,            /* a bounded device-side wait gave up */
+    BST_ERR_OUT_OF_MEMORY = 6       /* a plan-owned allocation failed */
+} bst_status_t;
+
+typedef enum {
+    BST_W_FILTER = 0,      /* FBP: P4 weight W[k] = g[k] (g = NULL: ramp, g = 1) */
+    BST_W_BACKPROJECT = 1  /* plain B: W[k] = 1/sigma_k = M dt / k, W[0] = 0 */
+} bst_mode_t;
+
+typedef struct bst_plan_s* bst_plan_t;
+typedef void* bst_stream_t;   /* a cudaStream_t; NULL is the legacy default stream */
+
+/* Create a plan for N = rays detector samples, V = angles projections and pad
+ * factor alpha.  angles_rad_host: host array of V float32 angles, copied.
+ * Builds the plan's device tables (twiddles, angle directions, bracket
+ * lookup) on the current device.  Errors: INVALID_ARGUMENT (null, V < 2,
+ * non-finite, unsorted or out-of-range angles), UNSUPPORTED_SIZE, CUDA,
+ * OUT_OF_MEMORY.  On error *plan is NULL. */
+bst_status_t bst_plan_create(bst_plan_t* plan, int rays, int angles,
+                             const float* angles_rad_host, int pad_factor);
+
+/* Free the plan's device tables (synchronises the device first). NULL is a no-op. */
+bst_status_t bst_plan_destroy(bst_plan_t plan);
+
+/* Device workspace in bytes that bst_fbp / bst_backproject need for `slices`
+ * slices: the padded polar spectrum Z[chunk][V][M] and the column-transformed
+ * grid T[chunk][N][M] (complex64) for a chunk of slice pairs sized to stay
+ * resident in L2 where possible.  0 for an invalid plan or slices <= 0. */
+size_t bst_workspace_bytes(bst_plan_t plan, int slices);
+
+/* BST filtered backprojection (Sec. 2 stages P0..P8 with the FBP weight
+ * x = B[F y], Sec. 1): volume[s] = FBP(sinogram[s]) for s < slices.
+ *   d_sino    [slices][V][N] float32, device
+ *   d_g       [M/2] float32 filter taps in BST form (g[k] = h^(sigma_k)/|sigma_k|),
+ *             device, or NULL for the ramp |sigma| (g = 1)
+ *   d_volume  [slices][N][N] float32, device, must not overlap d_sino
+ *   d_ws      device workspace of ws_bytes >= bst_workspace_bytes(plan, slices)
+ * Slices are transformed two at a time as the real and imaginary parts of
+ * one complex line; an odd last slice is paired with zeros.
+ * Errors: INVALID_ARGUMENT, WORKSPACE_TOO_SMALL, CUDA. */
+bst_status_t bst_fbp(bst_plan_t plan, const float* d_sino, int slices,
+                     const float* d_g, float* d_volume,
+                     void* d_ws, size_t ws_bytes, bst_stream_t stream);
+
+/* Plain BST backprojection b = B y via Eq. 3 (weight 1/sigma).  The DC bin
+ * is zero, so b is defined up to an additive constant (Eq. 3 holds for
+ * sigma > 0 only).  Arguments as bst_fbp. */
+bst_status_t bst_backproject(bst_plan_t plan, const float* d_sino, int slices,
+                             float* d_volume, void* d_ws, size_t ws_bytes,
+                             bst_stream_t stream);
+
+/* Device workspace in bytes for radon_adjoint and bst_fbp_filter_grad. */
+size_t bst_adjoint_workspace_bytes(bst_plan_t plan, int slices);
+
+/* Exact adjoint (transpose) of the discrete operator of bst_fbp (mode
+ * FILTER, taps d_g) or bst_backproject (mode BACKPROJECT, d_g ignored): a
+ * Fourier-slice projector (the FST dual of Sec. 2): 2D FFT of the zero-
+ * extended image, Cartesian-to-polar transpose of the bilinear gridding,
+ * weight, 1D inverse FFT along t, crop to N samples.
+ *   d_volume [slices][N][N] -> d_sino [slices][V][N], device float32.
+ * The first call builds the plan's cell lists of the gridding (device
+ * memory owned by the plan); it synchronises the stream.
+ * Errors: INVALID_ARGUMENT, WORKSPACE_TOO_SMALL, CUDA, OUT_OF_MEMORY. */
+bst_status_t radon_adjoint(bst_plan_t plan, bst_mode_t mode, const float* d_g,
+                           const float* d_volume, int slices, float* d_sino,
+                           void* d_ws, size_t ws_bytes, bst_stream_t stream);
+
+/* Gradient of sum(grad_vol * FBP(sino; g)) with respect to the M/2 filter
+ * taps g (the autograd backward of bst_fbp's d_g):
+ *   d_grad_g[m] = sum over slices, angles j and |k| = m of
+ *                 Re(conj(lambda_j[k]) * Y_j[k]),
+ * Y = dt * DFT of the padded rays, lambda = grad_vol pulled back through the
+ * crop, 2D transform, gridding and DC mean.  Deterministic (fixed reduction
+ * order).  d_grad_g is overwritten.  Workspace: bst_adjoint_workspace_bytes. */
+bst_status_t bst_fbp_filter_grad(bst_plan_t plan, const float* d_sino,
+                                 const float* d_grad_vol, int slices,
+                                 float* d_grad_g, void* d_ws, size_t ws_bytes,
+                                 bst_stream_t stream);
+
+/* Device workspace in bytes for brute_backproject with a filter (0 without). */
+size_t brute_workspace_bytes(bst_plan_t plan, int slices, int filtered);
+
+/* Slant-stack backprojection, the O(N^3)-per-slice comparator of Sec. 2:
+ * b[r][c] = sum_j w_j y_j(u . xi_j) with linear interpolation along t and
+ * trapezoid angular weights w_j = (theta_{j+1} - theta_{j-1})/2 (Eq. 2).
+ * d_g == NULL: plain B.  Otherwise each angle is first filtered along t with
+ * h_k = |sigma_k| g[k] (h_0 = dsigma/4 g[0], h_{M/2} = 0) on the plan's padded
+ * grid (SS filtered backprojection, x = B[F y]); the filtered sinogram goes
+ * to d_ws (brute_workspace_bytes(plan, slices, 1) bytes).
+ * Errors: INVALID_ARGUMENT, WORKSPACE_TOO_SMALL, CUDA. */
+bst_status_t brute_backproject(bst_plan_t plan, const float* d_sino, int slices,
+                               const float* d_g, float* d_volume,
+                               void* d_ws, size_t ws_bytes, bst_stream_t stream);
+
+/* Synchronise `stream` and return the plan's sticky device error (BST_OK if
+ * none, BST_ERR_CUDA if the stream reported an error). */
+bst_status_t bst_plan_status(bst_plan_t plan, bst_stream_t stream);
+
+/* Static English description of a status code. */
+const char* bst_status_string(bst_status_t status);
+
+/* FFT length M of a plan (0 for NULL). */
+int bst_plan_fft_length(bst_plan_t plan);
+
+/* Per-stage kernel timing (instrumentation, not part of the method).
+ * While enabled, every kernel launch of the plan is followed by a CUDA event
+ * record on its stream.  bst_plan_timing synchronises those events, adds the
+ * device time of each launch to stage_ms[stage] and its count to
+ * launches[stage] (arrays of n entries, n <= 8, caller-owned host memory),
+ * and clears the record.  Stages: 0 ray FFT + weight, 1 gridding + column
+ * inverse FFT, 2 row inverse FFT + crop, 3 slant-stack prefilter,
+ * 4 slant-stack backprojection, 5 adjoint row FFT, 6 adjoint column FFT,
+ * 7 adjoint polar gather + inverse FFT along t. */
+bst_status_t bst_plan_set_timing(bst_plan_t plan, int enable);
+bst_status_t bst_plan_timing(bst_plan_t plan, double* stage_ms, long long* launches, int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BST_H */

@@ -1,0 +1,52 @@
+"""ctypes loader of libbst.so: argument marshalling only, no computation.
+
+The library is built in-tree by ``paper_1704_08364_gb300.build``; loading
+fails loudly when it is missing (there is no fallback implementation)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbst.so")
+
+c_plan = ctypes.c_void_p
+c_ptr = ctypes.c_void_p
+c_int = ctypes.c_int
+c_size = ctypes.c_size_t
+
+# name -> (restype, argtypes); mirrors include/bst.h
+SIGNATURES = {
+    "bst_plan_create": (c_int, [ctypes.POINTER(c_plan), c_int, c_int, ctypes.POINTER(ctypes.c_float), c_int]),
+    "bst_plan_destroy": (c_int, [c_plan]),
+    "bst_workspace_bytes": (c_size, [c_plan, c_int]),
+    "bst_fbp": (c_int, [c_plan, c_ptr, c_int, c_ptr, c_ptr, c_ptr, c_size, c_ptr]),
+    "bst_backproject": (c_int, [c_plan, c_ptr, c_int, c_ptr, c_ptr, c_size, c_ptr]),
+    "bst_adjoint_workspace_bytes": (c_size, [c_plan, c_int]),
+    "radon_adjoint": (c_int, [c_plan, c_int, c_ptr, c_ptr, c_int, c_ptr, c_ptr, c_size, c_ptr]),
+    "bst_fbp_filter_grad": (c_int, [c_plan, c_ptr, c_ptr, c_int, c_ptr, c_ptr, c_size, c_ptr]),
+    "brute_workspace_bytes": (c_size, [c_plan, c_int, c_int]),
+    "brute_backproject": (c_int, [c_plan, c_ptr, c_int, c_ptr, c_ptr, c_ptr, c_size, c_ptr]),
+    "bst_plan_status": (c_int, [c_plan, c_ptr]),
+    "bst_status_string": (ctypes.c_char_p, [c_int]),
+    "bst_plan_fft_length": (c_int, [c_plan]),
+    "bst_plan_set_timing": (c_int, [c_plan, c_int]),
+    "bst_plan_timing": (c_int, [c_plan, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), c_int]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

@@ -1,0 +1,205 @@
+"""Python binding of libbst: the C-ABI calls of include/bst.h on torch tensors.
+
+Argument marshalling only: every step of the BST path runs in the library's
+CUDA kernels.  Tensors must be contiguous float32 CUDA tensors; work is
+enqueued on torch's current stream.  Workspaces are torch allocations owned
+by the Plan object and grown on demand.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+FILTER = 0
+BACKPROJECT = 1
+
+
+class BstError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.load().bst_status_string(code).decode()
+        super().__init__(f"{where}: {msg} (status {code})")
+        self.code = code
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise BstError(code, where)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _need(t, name, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+class Plan:
+    """A BST plan for N detector samples (rays), the given float32 angles in
+    [0, pi) (strictly increasing) and pad factor alpha (FFT length M = alpha N)."""
+
+    def __init__(self, rays: int, angles, pad_factor: int = 2):
+        lib = _lib.load()
+        th = np.ascontiguousarray(np.asarray(angles, dtype=np.float32))
+        h = ctypes.c_void_p()
+        _check(lib.bst_plan_create(ctypes.byref(h), int(rays), int(th.size),
+                                   th.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), int(pad_factor)),
+               "bst_plan_create")
+        self._h = h
+        self._lib = lib
+        self.rays = int(rays)
+        self.angles = th.copy()
+        self.V = int(th.size)
+        self.pad_factor = int(pad_factor)
+        self.M = lib.bst_plan_fft_length(h)
+        self._ws = {}
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                self._lib.bst_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def workspace(self, kind: str, nbytes: int, device) -> torch.Tensor:
+        key = (kind, str(device))
+        buf = self._ws.get(key)
+        if buf is None or buf.numel() < nbytes:
+            buf = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=device)
+            self._ws[key] = buf
+        return buf
+
+    def workspace_bytes(self, slices: int) -> int:
+        return int(self._lib.bst_workspace_bytes(self._h, int(slices)))
+
+    def adjoint_workspace_bytes(self, slices: int) -> int:
+        return int(self._lib.bst_adjoint_workspace_bytes(self._h, int(slices)))
+
+    def brute_workspace_bytes(self, slices: int, filtered: bool) -> int:
+        return int(self._lib.brute_workspace_bytes(self._h, int(slices), int(bool(filtered))))
+
+    def status(self):
+        _check(self._lib.bst_plan_status(self._h, _stream()), "bst_plan_status")
+
+    # -- forward -------------------------------------------------------------
+
+    def _forward(self, sino, g, out, mode):
+        _need(sino, "sino")
+        if sino.dim() == 2:
+            sino = sino.unsqueeze(0)
+        S = sino.shape[0]
+        _need(sino, "sino", (S, self.V, self.rays))
+        if g is not None:
+            _need(g, "g", (self.M // 2,))
+        if out is None:
+            out = torch.empty((S, self.rays, self.rays), dtype=torch.float32, device=sino.device)
+        _need(out, "out", (S, self.rays, self.rays))
+        nb = self.workspace_bytes(S)
+        ws = self.workspace("fwd", nb, sino.device)
+        if mode == FILTER:
+            code = self._lib.bst_fbp(self._h, _ptr(sino), S, _ptr(g), _ptr(out), _ptr(ws), ws.numel(), _stream())
+            _check(code, "bst_fbp")
+        else:
+            code = self._lib.bst_backproject(self._h, _ptr(sino), S, _ptr(out), _ptr(ws), ws.numel(), _stream())
+            _check(code, "bst_backproject")
+        return out
+
+    def fbp(self, sino, g=None, out=None):
+        """BST filtered backprojection of sino [S][V][N] -> [S][N][N]."""
+        return self._forward(sino, g, out, FILTER)
+
+    def backproject(self, sino, out=None):
+        """Plain BST backprojection (1/sigma weight, zero DC)."""
+        return self._forward(sino, None, out, BACKPROJECT)
+
+    def radon_adjoint(self, vol, mode: int = FILTER, g=None, out=None):
+        """Transpose of fbp (mode FILTER, taps g) or backproject (mode BACKPROJECT)."""
+        _need(vol, "vol")
+        if vol.dim() == 2:
+            vol = vol.unsqueeze(0)
+        S = vol.shape[0]
+        _need(vol, "vol", (S, self.rays, self.rays))
+        if g is not None:
+            _need(g, "g", (self.M // 2,))
+        if out is None:
+            out = torch.empty((S, self.V, self.rays), dtype=torch.float32, device=vol.device)
+        _need(out, "out", (S, self.V, self.rays))
+        nb = self.adjoint_workspace_bytes(S)
+        ws = self.workspace("adj", nb, vol.device)
+        _check(self._lib.radon_adjoint(self._h, int(mode), _ptr(g), _ptr(vol), S, _ptr(out), _ptr(ws), ws.numel(),
+                                       _stream()), "radon_adjoint")
+        return out
+
+    def filter_grad(self, sino, grad_vol, out=None):
+        """d/dg of sum(grad_vol * fbp(sino, g)) -> [M/2]."""
+        _need(sino, "sino")
+        _need(grad_vol, "grad_vol")
+        S = sino.shape[0]
+        _need(sino, "sino", (S, self.V, self.rays))
+        _need(grad_vol, "grad_vol", (S, self.rays, self.rays))
+        if out is None:
+            out = torch.empty((self.M // 2,), dtype=torch.float32, device=sino.device)
+        nb = self.adjoint_workspace_bytes(S)
+        ws = self.workspace("adj", nb, sino.device)
+        _check(self._lib.bst_fbp_filter_grad(self._h, _ptr(sino), _ptr(grad_vol), S, _ptr(out), _ptr(ws),
+                                             ws.numel(), _stream()), "bst_fbp_filter_grad")
+        return out
+
+    def brute_backproject(self, sino, g=None, out=None):
+        """Slant-stack backprojection (Eq. 2); with taps g, SS filtered backprojection."""
+        _need(sino, "sino")
+        if sino.dim() == 2:
+            sino = sino.unsqueeze(0)
+        S = sino.shape[0]
+        _need(sino, "sino", (S, self.V, self.rays))
+        if g is not None:
+            _need(g, "g", (self.M // 2,))
+        if out is None:
+            out = torch.empty((S, self.rays, self.rays), dtype=torch.float32, device=sino.device)
+        nb = self.brute_workspace_bytes(S, g is not None)
+        ws = self.workspace("brute", nb, sino.device) if nb > 0 else None
+        _check(self._lib.brute_backproject(self._h, _ptr(sino), S, _ptr(g), _ptr(out), _ptr(ws),
+                                           0 if ws is None else ws.numel(), _stream()), "brute_backproject")
+        return out
+
+
+class BstFbpFn(torch.autograd.Function):
+    """x = FBP(p; g) with gradients for the sinogram p and the filter taps g.
+    Backward: grad_p = radon_adjoint(grad_x) (the Fourier-slice transpose),
+    grad_g = filter_grad(p, grad_x); FFT intermediates are recomputed."""
+
+    @staticmethod
+    def forward(ctx, sino, g, plan: Plan):
+        ctx.plan = plan
+        ctx.save_for_backward(sino, g)
+        return plan.fbp(sino.contiguous(), g.contiguous())
+
+    @staticmethod
+    def backward(ctx, grad_x):
+        sino, g = ctx.saved_tensors
+        plan = ctx.plan
+        gx = grad_x.contiguous()
+        gp = plan.radon_adjoint(gx, FILTER, g) if ctx.needs_input_grad[0] else None
+        gg = plan.filter_grad(sino, gx) if ctx.needs_input_grad[1] else None
+        return gp, gg, None
+
+
+def fbp_autograd(sino, g, plan: Plan):
+    return BstFbpFn.apply(sino, g, plan)

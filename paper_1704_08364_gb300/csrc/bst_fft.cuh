@@ -1,0 +1,228 @@
+// bst_fft.cuh -- shared-memory Stockham FFT engine for one line of length M.
+//
+// Used by every stage of the BST path that transforms along a line: the 1D
+// FFT along the detector (stage P3), the column and row passes of the 2D
+// inverse FFT (stage P6) and their adjoints.  A line of M complex64 values
+// is transformed by TPL threads in log_R(M) radix-R Stockham passes
+// (out-of-order autosort: no bit reversal), in place in shared memory with a
+// barrier between the loads and the stores of each pass.  The first pass may
+// read from any source (global memory, a gather) and the last may write to
+// any sink, so loads and stores fuse with the neighbouring stage.
+//
+// Pass with sub-transform length NS and radix R, butterfly j in [0, M/R):
+//   inputs   x[j + s M/R],  s = 0..R-1
+//   twiddle  x_s *= w^(k s),  k = j mod NS,  w = exp(-+ 2 pi i / (NS R))
+//   DFT_R in registers
+//   outputs  y[(j / NS) NS R + k + s NS]
+// Forward transforms use exp(-2 pi i k m / M), inverse ones exp(+...), both
+// unnormalised.  Twiddles come from a table tw[m] = exp(-2 pi i m / M)
+// computed in double precision on the host.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace bst {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+// a * (sigma i), sigma = -1 forward, +1 inverse
+template <bool INV> __device__ __forceinline__ float2 mul_si(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// a * (c + sigma i d): multiplication by exp(sigma i phi) with c = cos phi, d = sin phi
+template <bool INV> __device__ __forceinline__ float2 mul_w(float2 a, float c, float d) {
+    const float sd = INV ? d : -d;
+    return make_float2(fmaf(a.x, c, -a.y * sd), fmaf(a.y, c, a.x * sd));
+}
+
+// cos and sin of pi/4, pi/8, 3 pi/8 and sqrt(3)/2
+#define BST_R2 0.70710678118654752440f
+#define BST_C8 0.92387953251128675613f
+#define BST_S8 0.38268343236508977173f
+#define BST_H3 0.86602540378443864676f
+
+template <int R, bool INV> struct Dft;
+
+template <bool INV> struct Dft<2, INV> {
+    __device__ __forceinline__ static void run(float2* a) {
+        const float2 t = a[1];
+        a[1] = csub(a[0], t);
+        a[0] = cadd(a[0], t);
+    }
+};
+
+template <bool INV> struct Dft<3, INV> {
+    __device__ __forceinline__ static void run(float2* a) {
+        const float2 t = cadd(a[1], a[2]);
+        const float2 u = csub(a[1], a[2]);
+        const float2 m = make_float2(fmaf(-0.5f, t.x, a[0].x), fmaf(-0.5f, t.y, a[0].y));
+        const float2 v = mul_si<INV>(cscale(u, BST_H3));
+        a[0] = cadd(a[0], t);
+        a[1] = cadd(m, v);
+        a[2] = csub(m, v);
+    }
+};
+
+template <bool INV> struct Dft<4, INV> {
+    __device__ __forceinline__ static void run(float2* a) {
+        const float2 a0 = cadd(a[0], a[2]), a1 = csub(a[0], a[2]);
+        const float2 b0 = cadd(a[1], a[3]), b1 = mul_si<INV>(csub(a[1], a[3]));
+        a[0] = cadd(a0, b0);
+        a[2] = csub(a0, b0);
+        a[1] = cadd(a1, b1);
+        a[3] = csub(a1, b1);
+    }
+};
+
+template <bool INV> struct Dft<8, INV> {
+    __device__ __forceinline__ static void run(float2* a) {
+        float2 e[4] = {a[0], a[2], a[4], a[6]};
+        float2 o[4] = {a[1], a[3], a[5], a[7]};
+        Dft<4, INV>::run(e);
+        Dft<4, INV>::run(o);
+        o[1] = mul_w<INV>(o[1], BST_R2, BST_R2);
+        o[2] = mul_si<INV>(o[2]);
+        o[3] = mul_w<INV>(o[3], -BST_R2, BST_R2);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            a[k] = cadd(e[k], o[k]);
+            a[k + 4] = csub(e[k], o[k]);
+        }
+    }
+};
+
+template <bool INV> struct Dft<16, INV> {
+    __device__ __forceinline__ static void run(float2* a) {
+        float2 e[8], o[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            e[k] = a[2 * k];
+            o[k] = a[2 * k + 1];
+        }
+        Dft<8, INV>::run(e);
+        Dft<8, INV>::run(o);
+        o[1] = mul_w<INV>(o[1], BST_C8, BST_S8);
+        o[2] = mul_w<INV>(o[2], BST_R2, BST_R2);
+        o[3] = mul_w<INV>(o[3], BST_S8, BST_C8);
+        o[4] = mul_si<INV>(o[4]);
+        o[5] = mul_w<INV>(o[5], -BST_S8, BST_C8);
+        o[6] = mul_w<INV>(o[6], -BST_R2, BST_R2);
+        o[7] = mul_w<INV>(o[7], -BST_C8, BST_S8);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            a[k] = cadd(e[k], o[k]);
+            a[k + 8] = csub(e[k], o[k]);
+        }
+    }
+};
+
+// ---- radix schedule --------------------------------------------------------
+
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
+// Radix of pass p for length M = 3^b 2^a (b <= 1): one radix-3 pass first,
+// then ceil(a/4) power-of-two passes of as equal a size as possible.
+__host__ __device__ constexpr int radix_of(int M, int p) {
+    const bool three = (M % 3 == 0);
+    if (three && p == 0) return 3;
+    const int a = ilog2c(three ? M / 3 : M);
+    const int passes = (a + 3) / 4;
+    const int q = p - (three ? 1 : 0);
+    const int bits = a / passes + (q < a % passes ? 1 : 0);
+    return 1 << bits;
+}
+
+// ---- line storage ----------------------------------------------------------
+
+// Shared-memory line with one padding slot per 16 elements (bank-conflict free
+// for the strided stores of the early passes).
+__host__ __device__ constexpr int smem_line_len(int M) { return M + M / 16; }
+
+struct SmemLine {
+    float2* p;
+    static constexpr bool kSmem = true;
+    __device__ __forceinline__ float2 load(int i) const { return p[i + (i >> 4)]; }
+    __device__ __forceinline__ void store(int i, float2 v) const { p[i + (i >> 4)] = v; }
+};
+
+// ---- passes ----------------------------------------------------------------
+
+template <int M, int R, int NS, int TPL, bool INV, class Src, class Dst>
+__device__ __forceinline__ void stockham_pass(int t, const Src& src, const Dst& dst,
+                                              const float2* __restrict__ tw, bool sync_mid) {
+    constexpr int NB = M / R;
+    constexpr int IT = (NB + TPL - 1) / TPL;
+    float2 a[IT][R];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int j = t + it * TPL;
+        if ((NB % TPL) == 0 || j < NB) {
+#pragma unroll
+            for (int s = 0; s < R; ++s) a[it][s] = src.load(j + s * NB);
+        }
+    }
+    if (sync_mid) __syncthreads();
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int j = t + it * TPL;
+        if ((NB % TPL) == 0 || j < NB) {
+            const int k = (NS == 1) ? 0 : (j % NS);
+            if (NS > 1) {
+                constexpr int STEP = M / (NS * R);
+#pragma unroll
+                for (int s = 1; s < R; ++s) {
+                    const float2 w = __ldg(tw + k * s * STEP);
+                    a[it][s] = INV ? cmulc(a[it][s], w) : cmul(a[it][s], w);
+                }
+            }
+            Dft<R, INV>::run(a[it]);
+            const int base = (j / NS) * NS * R + k;
+#pragma unroll
+            for (int s = 0; s < R; ++s) dst.store(base + s * NS, a[it][s]);
+        }
+    }
+}
+
+// Run passes PIDX.. of the length-M transform.  Pass 0 reads `src`, the last
+// pass writes `dst`; the others go through the shared-memory line `sm`.
+// Every thread of the block must call this (it contains __syncthreads()).
+template <int M, int TPL, bool INV, int PIDX, int NS, class Src, class Dst>
+__device__ __forceinline__ void fft_run(int t, const Src& src, const Dst& dst, const SmemLine& sm,
+                                        const float2* __restrict__ tw) {
+    constexpr int R = radix_of(M, PIDX);
+    constexpr bool LAST = (NS * R == M);
+    if constexpr (PIDX == 0) {
+        if constexpr (LAST) {
+            stockham_pass<M, R, NS, TPL, INV>(t, src, dst, tw, Src::kSmem && Dst::kSmem);
+        } else {
+            stockham_pass<M, R, NS, TPL, INV>(t, src, sm, tw, Src::kSmem);
+            __syncthreads();
+            fft_run<M, TPL, INV, PIDX + 1, NS * R>(t, src, dst, sm, tw);
+        }
+    } else {
+        if constexpr (LAST) {
+            stockham_pass<M, R, NS, TPL, INV>(t, sm, dst, tw, Dst::kSmem);
+        } else {
+            stockham_pass<M, R, NS, TPL, INV>(t, sm, sm, tw, true);
+            __syncthreads();
+            fft_run<M, TPL, INV, PIDX + 1, NS * R>(t, src, dst, sm, tw);
+        }
+    }
+}
+
+template <int M, int TPL, bool INV, class Src, class Dst>
+__device__ __forceinline__ void fft_line(int t, const Src& src, const Dst& dst, const SmemLine& sm,
+                                         const float2* __restrict__ tw) {
+    fft_run<M, TPL, INV, 0, 1>(t, src, dst, sm, tw);
+}
+
+// signed frequency of natural-order index p
+__device__ __forceinline__ int signed_freq(int p, int M) { return p < (M >> 1) ? p : p - M; }
+
+}  // namespace bst

@@ -1,0 +1,91 @@
+// bst_internal.h -- plan object and host-side helpers shared by the
+// translation units of libbst (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/bst.h"
+#include "bst_geo.cuh"
+
+struct bst_plan_s {
+    int N = 0, V = 0, M = 0, alpha = 0;
+    int device = 0;
+    std::vector<double> theta;      // angles as given (float32 widened exactly)
+    // device tables owned by the plan
+    float2* tw = nullptr;           // [M] exp(-2 pi i m / M)
+    float4* dir = nullptr;          // [V+2] angle directions, double-float
+    float* invdth = nullptr;        // [V+1]
+    int* lut = nullptr;             // [L]
+    int L = 0;
+    float lut_scale = 0.f;
+    double2* cs64 = nullptr;        // [V] (cos, sin) in double, slant-stack tile origins
+    float2* cs32 = nullptr;         // [V] (cos, sin) in float, slant-stack tile offsets
+    float* wq = nullptr;            // [V] trapezoid weights of Eq. 2
+    int* err = nullptr;             // sticky device error word
+    int chunk_pairs = 1;            // slice pairs per chunk of the forward path
+    // gridding cell lists for the adjoint, built on first use
+    int* cell_start = nullptr;      // [(V+1) M + 1]
+    int* cell_pts = nullptr;        // [n] index c * M + r of each Cartesian point
+    float2* cell_w = nullptr;       // [n] (fth, frac) of each point
+    int cell_n = 0;
+    bool cells_built = false;
+    // optional per-stage timing: an event after every launch (see bst_plan_set_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_stage;     // stage that ended at each recorded event (-1: start mark)
+    size_t ev_used = 0;
+    double stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long stage_launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+
+    bst::Geo geo() const {
+        bst::Geo g;
+        g.dir = dir;
+        g.invdth = invdth;
+        g.lut = lut;
+        g.V = V;
+        g.M = M;
+        g.L = L;
+        g.lut_scale = lut_scale;
+        return g;
+    }
+};
+
+namespace bsth {
+
+inline bool supported_fft_length(int M) {
+    int m = M;
+    if (m % 3 == 0) m /= 3;
+    if (m < 16 || (m & (m - 1)) != 0) return false;
+    return M >= 16 && M <= 4096;
+}
+
+inline bool check_cuda(cudaError_t e) { return e == cudaSuccess; }
+
+// byte sizes of the per-pair workspace of the forward path
+inline size_t fwd_bytes_per_pair(const bst_plan_s* p) {
+    const size_t rows_t = (size_t)((p->N + 3) / 4) * 4;
+    return ((size_t)p->V * p->M + rows_t * p->M) * sizeof(float2);
+}
+
+}  // namespace bsth
+
+// Record a timing mark on `st` after a launch of `stage` (or a start mark
+// with stage -1).  No-op unless timing is enabled on the plan.
+void bst_timing_mark(bst_plan_s* p, cudaStream_t st, int stage);
+
+// launchers (one dispatch on M each), defined in the kernel translation units
+bst_status_t bst_launch_forward(bst_plan_s* p, const float* sino, int slices, int mode, const float* g,
+                                float* vol, void* ws, size_t ws_bytes, cudaStream_t st);
+bst_status_t bst_launch_adjoint(bst_plan_s* p, int mode, const float* g, const float* vol, int slices,
+                                float* sino, void* ws, size_t ws_bytes, cudaStream_t st);
+bst_status_t bst_launch_filter_grad(bst_plan_s* p, const float* sino, const float* gvol, int slices,
+                                    float* grad_g, void* ws, size_t ws_bytes, cudaStream_t st);
+bst_status_t bst_launch_brute(bst_plan_s* p, const float* sino, int slices, const float* g, float* vol,
+                              void* ws, size_t ws_bytes, cudaStream_t st);
+bst_status_t bst_build_cells(bst_plan_s* p, cudaStream_t st);
+size_t bst_adjoint_ws(const bst_plan_s* p, int slices);
+size_t bst_brute_ws(const bst_plan_s* p, int slices, int filtered);
+
+// mode values shared by the launchers
+enum { BSTK_FILTER = 0, BSTK_BACKPROJECT = 1, BSTK_RAW = 2 };

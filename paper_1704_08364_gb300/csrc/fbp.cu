@@ -1,0 +1,326 @@
+// fbp.cu -- the BST forward path (bst_fbp, bst_backproject) on sm_103a.
+//
+// Per pair of slices (packed as the real and imaginary parts of one complex
+// line, so every FFT is a full complex transform with no waste):
+//
+//   k_ray_fft   stages P2 + P3 + P4: load each angle's rays with centre-aligned
+//               zero padding to M, forward FFT along t in shared memory,
+//               multiply by the weight W[|k|], write Z[V][M].
+//   k_grid_col  stages P0 + P5 + the column half of P6: for one Cartesian
+//               column c' and its mirror -c', compute the polar coordinates of
+//               every point once, gather the four bilinear taps from Z for both
+//               points (gather form, no atomics), inverse FFT along r' in
+//               shared memory, keep the N central rows, write T.
+//   k_row_ifft  the row half of P6 + P7 + P8: inverse FFT along c' for four
+//               rows at a time, keep the N central columns, scale by
+//               dt dw^2 = N / (2 M^2), write Re to slice a and Im to slice b.
+//
+// Z and T live in a caller-provided workspace sized for a chunk of pairs
+// that fits in L2 where possible (one pair at N = 2048: 2 x 64 MiB).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "bst_fft.cuh"
+#include "bst_geo.cuh"
+#include "bst_internal.h"
+
+namespace bst {
+
+// threads per line: 16 elements per thread (12 for lengths 3 * 2^a)
+template <int M> __host__ __device__ constexpr int tpl_of() { return (M % 3 == 0) ? M / 12 : M / 16; }
+
+// ---------------------------------------------------------------------------
+// k_ray_fft
+
+struct RaySrc {
+    const float* ya;
+    const float* yb;
+    int N, M;
+    bool live;
+    static constexpr bool kSmem = false;
+    __device__ __forceinline__ float2 load(int m) const {
+        int i = m + (N >> 1);
+        if (i >= M) i -= M;
+        if (!live || i >= N) return make_float2(0.f, 0.f);
+        return make_float2(__ldg(ya + i), yb ? __ldg(yb + i) : 0.f);
+    }
+};
+
+struct SpecDst {
+    float2* z;
+    const float* g;
+    int M, mode;
+    float two_alpha;
+    bool live;
+    static constexpr bool kSmem = false;
+    __device__ __forceinline__ void store(int k, float2 v) const {
+        if (!live) return;
+        const int ak = k <= (M >> 1) ? k : M - k;
+        float w;
+        if (mode == BSTK_RAW) w = 1.f;
+        else if (ak == (M >> 1)) w = 0.f;
+        else if (mode == BSTK_FILTER) w = g ? __ldg(g + ak) : 1.f;
+        else w = ak == 0 ? 0.f : __fdiv_rn(two_alpha, (float)ak);
+        z[k] = make_float2(v.x * w, v.y * w);
+    }
+};
+
+template <int M, int TPL, int LPC>
+__global__ void __launch_bounds__(TPL * LPC)
+    k_ray_fft(const float* __restrict__ sino, int slices, int pair0, int N, int V, int mode,
+              const float* __restrict__ g, float two_alpha, float2* __restrict__ Z, const float2* __restrict__ tw) {
+    extern __shared__ float2 smem[];
+    const int line = threadIdx.x / TPL, t = threadIdx.x % TPL;
+    const int j = blockIdx.x * LPC + line;
+    const int pl = blockIdx.y;
+    const int sa = 2 * (pair0 + pl), sb = sa + 1;
+    const bool live = j < V;
+    const int jj = live ? j : 0;
+    RaySrc src{sino + ((size_t)sa * V + jj) * N, sb < slices ? sino + ((size_t)sb * V + jj) * N : nullptr, N, M,
+               live};
+    SpecDst dst{Z + ((size_t)pl * V + jj) * M, g, M, mode, two_alpha, live};
+    SmemLine sm{smem + line * smem_line_len(M)};
+    fft_line<M, TPL, false>(t, src, dst, sm, tw);
+}
+
+// ---------------------------------------------------------------------------
+// k_grid_col
+
+// T layout per pair: [ceil(N/4)][M][4] complex, row r of the kept band at
+// (r / 4, c', r % 4): a column write fills whole 32-byte sectors and a
+// four-row block is contiguous for k_row_ifft.
+struct ColDst {
+    float2* T;
+    int N, M, cidx;
+    bool rev, live;
+    static constexpr bool kSmem = false;
+    __device__ __forceinline__ void store(int p, float2 v) const {
+        if (!live) return;
+        const int q = rev ? (p == 0 ? 0 : M - p) : p;
+        const int r = signed_freq(q, M) + (N >> 1);
+        if (r < 0 || r >= N) return;
+        T[((size_t)(r >> 2) * M + cidx) * 4 + (r & 3)] = v;
+    }
+};
+
+template <int M, int TPL, int CPC>
+__global__ void __launch_bounds__(2 * TPL * CPC)
+    k_grid_col(const float2* __restrict__ Z, int V, int N, Geo geo, float2* __restrict__ T,
+               const float2* __restrict__ tw) {
+    extern __shared__ float2 smem[];
+    const int pl = blockIdx.y;
+    const float2* Zp = Z + (size_t)pl * V * M;
+    float2* Tp = T + (size_t)pl * ((N + 3) / 4) * 4 * M;
+    const int cp = threadIdx.x / (2 * TPL);
+    const int lt = threadIdx.x % (2 * TPL);
+    const int q = blockIdx.x * CPC + cp;
+    const bool live = q < (M >> 1);
+    const SmemLine smA{smem + (2 * cp) * smem_line_len(M)};
+    const SmemLine smB{smem + (2 * cp + 1) * smem_line_len(M)};
+    // P0 + P5: polar coordinates once per point, taps for (q, r') and (-q, -r');
+    // the mirror column is stored index-reversed (its transform is read back reversed)
+    for (int ridx = lt; ridx < M; ridx += 2 * TPL) {
+        float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
+        if (live) {
+            const int ry = signed_freq(ridx, M);
+            Polar P;
+            if (!(q == 0 && ry == 0) && polar_of(q, ry, geo, P)) {
+                int K0;
+                float fk;
+                radial_bin(P, P.up, K0, fk);
+                va = polar_gather(Zp, V, M, P.J, P.fth, K0, fk);
+                if (q != 0) {
+                    radial_bin(P, !P.up, K0, fk);
+                    vb = polar_gather(Zp, V, M, P.J, P.fth, K0, fk);
+                }
+            }
+        }
+        smA.store(ridx, va);
+        smB.store(ridx, vb);
+    }
+    // the origin is single-valued: mean over angles of the DC bin
+    if (live && q == 0) {
+        if constexpr (2 * TPL >= 32) {
+            if (lt < 32) {
+                float sx = 0.f, sy = 0.f;
+                for (int j = lt; j < V; j += 32) {
+                    const float2 z = __ldg(Zp + (size_t)j * M);
+                    sx += z.x;
+                    sy += z.y;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                }
+                if (lt == 0) smA.store(0, make_float2(sx / (float)V, sy / (float)V));
+            }
+        } else {
+            if (lt == 0) {
+                float sx = 0.f, sy = 0.f;
+                for (int j = 0; j < V; ++j) {
+                    const float2 z = __ldg(Zp + (size_t)j * M);
+                    sx += z.x;
+                    sy += z.y;
+                }
+                smA.store(0, make_float2(sx / (float)V, sy / (float)V));
+            }
+        }
+    }
+    __syncthreads();
+    const int half = lt / TPL;
+    const int t = lt % TPL;
+    const SmemLine sm = half ? smB : smA;
+    const int cidx = half ? (q == 0 ? (M >> 1) : M - q) : q;
+    ColDst dst{Tp, N, M, cidx, half != 0 && q != 0, live};
+    fft_line<M, TPL, true>(t, sm, dst, sm, tw);
+}
+
+// ---------------------------------------------------------------------------
+// k_row_ifft
+
+struct TileSrc {
+    const float2* T;
+    int M, rb, line;
+    bool live;
+    static constexpr bool kSmem = false;
+    __device__ __forceinline__ float2 load(int c) const {
+        return live ? __ldg(T + ((size_t)rb * M + c) * 4 + line) : make_float2(0.f, 0.f);
+    }
+};
+
+struct VolDst {
+    float* va;
+    float* vb;
+    int N, M;
+    float scale;
+    bool live;
+    static constexpr bool kSmem = false;
+    __device__ __forceinline__ void store(int p, float2 v) const {
+        if (!live) return;
+        const int c = signed_freq(p, M) + (N >> 1);
+        if (c < 0 || c >= N) return;
+        va[c] = v.x * scale;
+        if (vb) vb[c] = v.y * scale;
+    }
+};
+
+template <int M> __host__ __device__ constexpr int row_line_stride() { return smem_line_len(M) + 4; }
+
+template <int M, int TPL, int TPC>
+__global__ void __launch_bounds__(4 * TPL * TPC)
+    k_row_ifft(const float2* __restrict__ T, int slices, int pair0, int N, float scale, float* __restrict__ vol,
+               const float2* __restrict__ tw) {
+    extern __shared__ float2 smem[];
+    const int pl = blockIdx.y;
+    const int tile = threadIdx.x / (4 * TPL);
+    const int w = threadIdx.x % (4 * TPL);
+    const int line = w & 3, t = w >> 2;
+    const int rb = blockIdx.x * TPC + tile;
+    const int r = rb * 4 + line;
+    const bool live = r < N;
+    const int rr = live ? r : 0;
+    const float2* Tp = T + (size_t)pl * ((N + 3) / 4) * 4 * M;
+    const int sa = 2 * (pair0 + pl), sb = sa + 1;
+    TileSrc src{Tp, M, live ? rb : 0, line, live};
+    VolDst dst{vol + ((size_t)sa * N + rr) * N, sb < slices ? vol + ((size_t)sb * N + rr) * N : nullptr, N, M,
+               scale, live};
+    SmemLine sm{smem + (tile * 4 + line) * row_line_stride<M>()};
+    fft_line<M, TPL, true>(t, src, dst, sm, tw);
+}
+
+// ---------------------------------------------------------------------------
+// host launcher
+
+template <class K>
+static bool set_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return true;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
+}
+
+template <int M> struct FwdCfg {
+    static constexpr int TPL = tpl_of<M>();
+    static constexpr int LPC1 = (256 / TPL) > 1 ? 256 / TPL : 1;
+    static constexpr int CPC = (128 / (2 * TPL)) > 1 ? 128 / (2 * TPL) : 1;
+    static constexpr int TPC = (128 / (4 * TPL)) > 1 ? 128 / (4 * TPL) : 1;
+    static constexpr size_t S1 = (size_t)LPC1 * smem_line_len(M) * sizeof(float2);
+    static constexpr size_t S2 = (size_t)2 * CPC * smem_line_len(M) * sizeof(float2);
+    static constexpr size_t S3 = (size_t)4 * TPC * row_line_stride<M>() * sizeof(float2);
+};
+
+template <int M>
+bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int mode, const float* g, float* vol,
+                              void* ws, cudaStream_t st) {
+    using C = FwdCfg<M>;
+    static bool attr_ok = set_smem(k_ray_fft<M, C::TPL, C::LPC1>, C::S1) &&
+                          set_smem(k_grid_col<M, C::TPL, C::CPC>, C::S2) &&
+                          set_smem(k_row_ifft<M, C::TPL, C::TPC>, C::S3);
+    if (!attr_ok) return BST_ERR_CUDA;
+    const int N = p->N, V = p->V;
+    const int pairs = (slices + 1) / 2;
+    const int chunk = std::min(pairs, p->chunk_pairs);
+    float2* Z = (float2*)ws;
+    float2* T = Z + (size_t)chunk * V * M;
+    const float scale = (float)((double)N / (2.0 * (double)M * (double)M));
+    const float two_alpha = (float)(2 * p->alpha);
+    const bst::Geo geo = p->geo();
+    const int row_tiles = (N + 3) / 4;
+    for (int p0 = 0; p0 < pairs; p0 += chunk) {
+        const int np = std::min(chunk, pairs - p0);
+        bst_timing_mark(p, st, -1);
+        k_ray_fft<M, C::TPL, C::LPC1><<<dim3((V + C::LPC1 - 1) / C::LPC1, np), C::TPL * C::LPC1, C::S1, st>>>(
+            sino, slices, p0, N, V, mode, g, two_alpha, Z, p->tw);
+        bst_timing_mark(p, st, 0);
+        k_grid_col<M, C::TPL, C::CPC><<<dim3((M / 2 + C::CPC - 1) / C::CPC, np), 2 * C::TPL * C::CPC, C::S2, st>>>(
+            Z, V, N, geo, T, p->tw);
+        bst_timing_mark(p, st, 1);
+        k_row_ifft<M, C::TPL, C::TPC><<<dim3((row_tiles + C::TPC - 1) / C::TPC, np), 4 * C::TPL * C::TPC, C::S3, st>>>(
+            T, slices, p0, N, scale, vol, p->tw);
+        bst_timing_mark(p, st, 2);
+    }
+    return cudaGetLastError() == cudaSuccess ? BST_OK : BST_ERR_CUDA;
+}
+
+}  // namespace bst
+
+#define BST_FOR_EACH_M(X) \
+    X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(48) X(96) X(192) X(384) X(768) X(1536) X(3072)
+
+bst_status_t bst_launch_forward(bst_plan_s* p, const float* sino, int slices, int mode, const float* g, float* vol,
+                                void* ws, size_t /*ws_bytes*/, cudaStream_t st) {
+    switch (p->M) {
+#define BST_CASE(m) \
+    case m: return bst::launch_forward_M<m>(p, sino, slices, mode, g, vol, ws, st);
+        BST_FOR_EACH_M(BST_CASE)
+#undef BST_CASE
+    }
+    return BST_ERR_UNSUPPORTED_SIZE;
+}
+
+namespace bst {
+template <int M>
+bst_status_t launch_ray_spectrum_M(bst_plan_s* p, const float* sino, int slices, int p0, int np, float2* Y,
+                                   cudaStream_t st) {
+    using C = FwdCfg<M>;
+    static bool attr_ok = set_smem(k_ray_fft<M, C::TPL, C::LPC1>, C::S1);
+    if (!attr_ok) return BST_ERR_CUDA;
+    bst_timing_mark(p, st, -1);
+    k_ray_fft<M, C::TPL, C::LPC1><<<dim3((p->V + C::LPC1 - 1) / C::LPC1, np), C::TPL * C::LPC1, C::S1, st>>>(
+        sino, slices, p0, p->N, p->V, BSTK_RAW, nullptr, 0.f, Y, p->tw);
+    bst_timing_mark(p, st, 0);
+    return BST_OK;
+}
+}  // namespace bst
+
+// Y[pair][V][M] = unscaled DFT of the padded rays of pairs [p0, p0 + np), no weight
+bst_status_t bst_launch_ray_spectrum(bst_plan_s* p, const float* sino, int slices, int p0, int np, float2* Y,
+                                     cudaStream_t st) {
+    switch (p->M) {
+#define BST_CASE(m) \
+    case m: return bst::launch_ray_spectrum_M<m>(p, sino, slices, p0, np, Y, st);
+        BST_FOR_EACH_M(BST_CASE)
+#undef BST_CASE
+    }
+    return BST_ERR_UNSUPPORTED_SIZE;
+}

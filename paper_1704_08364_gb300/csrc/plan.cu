@@ -1,0 +1,279 @@
+// plan.cu -- plan creation (device tables), argument validation and the
+// public entry points of libbst.  The kernels live in fbp.cu (forward BST),
+// adjoint.cu (Fourier-slice adjoint and filter gradient) and brute.cu
+// (slant-stack comparator).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bst_internal.h"
+
+namespace {
+
+template <class T>
+bool upload(T** dptr, const std::vector<T>& host) {
+    if (cudaMalloc((void**)dptr, host.size() * sizeof(T)) != cudaSuccess) return false;
+    return cudaMemcpy(*dptr, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+void free_plan(bst_plan_s* p) {
+    if (!p) return;
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    cudaFree(p->tw);
+    cudaFree(p->dir);
+    cudaFree(p->invdth);
+    cudaFree(p->lut);
+    cudaFree(p->cs64);
+    cudaFree(p->cs32);
+    cudaFree(p->wq);
+    cudaFree(p->err);
+    cudaFree(p->cell_start);
+    cudaFree(p->cell_pts);
+    cudaFree(p->cell_w);
+    delete p;
+}
+
+float4 split_dir(double c, double s) {
+    const float ch = (float)c, sh = (float)s;
+    return make_float4(ch, (float)(c - (double)ch), sh, (float)(s - (double)sh));
+}
+
+bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
+    const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+    return a0 < b0 + nb && b0 < a0 + na;
+}
+
+}  // namespace
+
+void bst_timing_mark(bst_plan_s* p, cudaStream_t st, int stage) {
+    if (!p->timing) return;
+    if (p->ev_used == p->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        p->ev_pool.push_back(e);
+        p->ev_stage.push_back(-1);
+    }
+    p->ev_stage[p->ev_used] = stage;
+    cudaEventRecord(p->ev_pool[p->ev_used], st);
+    ++p->ev_used;
+}
+
+extern "C" {
+
+bst_status_t bst_plan_set_timing(bst_plan_t p, int enable) {
+    if (!p) return BST_ERR_INVALID_ARGUMENT;
+    p->timing = enable != 0;
+    return BST_OK;
+}
+
+bst_status_t bst_plan_timing(bst_plan_t p, double* stage_ms, long long* launches, int n) {
+    if (!p || n < 0 || n > 8 || (n > 0 && (!stage_ms || !launches))) return BST_ERR_INVALID_ARGUMENT;
+    for (size_t i = 0; i < p->ev_used; ++i)
+        if (cudaEventSynchronize(p->ev_pool[i]) != cudaSuccess) return BST_ERR_CUDA;
+    for (size_t i = 1; i < p->ev_used; ++i) {
+        const int s = p->ev_stage[i];
+        if (s < 0) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p->ev_pool[i - 1], p->ev_pool[i]) != cudaSuccess) return BST_ERR_CUDA;
+        if (s < 8) {
+            p->stage_ms[s] += ms;
+            p->stage_launches[s] += 1;
+        }
+    }
+    for (int s = 0; s < n; ++s) {
+        stage_ms[s] = p->stage_ms[s];
+        launches[s] = p->stage_launches[s];
+    }
+    for (int s = 0; s < 8; ++s) {
+        p->stage_ms[s] = 0.0;
+        p->stage_launches[s] = 0;
+    }
+    p->ev_used = 0;
+    return BST_OK;
+}
+
+const char* bst_status_string(bst_status_t s) {
+    switch (s) {
+        case BST_OK: return "ok";
+        case BST_ERR_INVALID_ARGUMENT: return "invalid argument";
+        case BST_ERR_UNSUPPORTED_SIZE: return "unsupported size (FFT length M = alpha N must be 2^a in [16, 4096] or 3*2^a in [48, 3072], N even)";
+        case BST_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+        case BST_ERR_CUDA: return "CUDA error";
+        case BST_ERR_TIMEOUT: return "device-side wait timed out";
+        case BST_ERR_OUT_OF_MEMORY: return "out of device memory";
+    }
+    return "unknown status";
+}
+
+bst_status_t bst_plan_create(bst_plan_t* out, int rays, int angles, const float* angles_rad_host, int pad_factor) {
+    if (!out) return BST_ERR_INVALID_ARGUMENT;
+    *out = nullptr;
+    if (!angles_rad_host || angles < 2 || rays < 2) return BST_ERR_INVALID_ARGUMENT;
+    if (pad_factor != 1 && pad_factor != 2) return BST_ERR_UNSUPPORTED_SIZE;
+    if (rays % 2 != 0) return BST_ERR_UNSUPPORTED_SIZE;
+    const int M = pad_factor * rays;
+    if (!bsth::supported_fft_length(M)) return BST_ERR_UNSUPPORTED_SIZE;
+    std::vector<double> th(angles);
+    for (int j = 0; j < angles; ++j) {
+        const double v = (double)angles_rad_host[j];
+        if (!std::isfinite(v) || v < 0.0 || v >= M_PI) return BST_ERR_INVALID_ARGUMENT;
+        if (j > 0 && !(v > th[j - 1])) return BST_ERR_INVALID_ARGUMENT;
+        th[j] = v;
+    }
+    bst_plan_s* p = new (std::nothrow) bst_plan_s();
+    if (!p) return BST_ERR_OUT_OF_MEMORY;
+    p->N = rays;
+    p->V = angles;
+    p->M = M;
+    p->alpha = pad_factor;
+    p->theta = th;
+    cudaGetDevice(&p->device);
+    const int V = angles;
+
+    std::vector<float2> tw(M);
+    for (int m = 0; m < M; ++m) {
+        const double a = -2.0 * M_PI * (double)m / (double)M;
+        tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    std::vector<double> ext(V + 2);
+    ext[0] = th[V - 1] - M_PI;
+    for (int j = 0; j < V; ++j) ext[j + 1] = th[j];
+    ext[V + 1] = th[0] + M_PI;
+    std::vector<float4> dir(V + 2);
+    for (int j = 0; j < V; ++j) dir[j + 1] = split_dir(std::cos(th[j]), std::sin(th[j]));
+    dir[0] = split_dir(-std::cos(th[V - 1]), -std::sin(th[V - 1]));
+    dir[V + 1] = split_dir(-std::cos(th[0]), -std::sin(th[0]));
+    std::vector<float> invdth(V + 1);
+    for (int J = -1; J <= V - 1; ++J) invdth[J + 1] = (float)(1.0 / (ext[J + 2] - ext[J + 1]));
+    const int L = std::max(64, 4 * V);
+    std::vector<int> lut(L);
+    {
+        int cnt = 0;
+        for (int b = 0; b < L; ++b) {
+            const double start = (double)b * M_PI / (double)L;
+            while (cnt < V && th[cnt] <= start) ++cnt;
+            lut[b] = cnt - 1;
+        }
+    }
+    std::vector<double2> cs64(V);
+    std::vector<float2> cs32(V);
+    std::vector<float> wq(V);
+    for (int j = 0; j < V; ++j) {
+        cs64[j] = make_double2(std::cos(th[j]), std::sin(th[j]));
+        cs32[j] = make_float2((float)cs64[j].x, (float)cs64[j].y);
+        wq[j] = (float)((ext[j + 2] - ext[j]) / 2.0);
+    }
+    p->L = L;
+    p->lut_scale = (float)((double)L / M_PI);
+    bool ok = upload(&p->tw, tw) && upload(&p->dir, dir) && upload(&p->invdth, invdth) && upload(&p->lut, lut) &&
+              upload(&p->cs64, cs64) && upload(&p->cs32, cs32) && upload(&p->wq, wq);
+    if (ok) ok = cudaMalloc((void**)&p->err, sizeof(int)) == cudaSuccess && cudaMemset(p->err, 0, sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_plan(p);
+        return BST_ERR_OUT_OF_MEMORY;
+    }
+    const size_t per_pair = bsth::fwd_bytes_per_pair(p);
+    const size_t budget = (size_t)64 << 20;
+    p->chunk_pairs = (int)std::max<size_t>(1, std::min<size_t>(256, budget / per_pair));
+    *out = p;
+    return BST_OK;
+}
+
+bst_status_t bst_plan_destroy(bst_plan_t p) {
+    if (!p) return BST_OK;
+    cudaDeviceSynchronize();
+    free_plan(p);
+    return BST_OK;
+}
+
+int bst_plan_fft_length(bst_plan_t p) { return p ? p->M : 0; }
+
+size_t bst_workspace_bytes(bst_plan_t p, int slices) {
+    if (!p || slices <= 0) return 0;
+    const int pairs = (slices + 1) / 2;
+    return (size_t)std::min(pairs, p->chunk_pairs) * bsth::fwd_bytes_per_pair(p);
+}
+
+size_t bst_adjoint_workspace_bytes(bst_plan_t p, int slices) {
+    if (!p || slices <= 0) return 0;
+    return bst_adjoint_ws(p, slices);
+}
+
+size_t brute_workspace_bytes(bst_plan_t p, int slices, int filtered) {
+    if (!p || slices <= 0) return 0;
+    return bst_brute_ws(p, slices, filtered);
+}
+
+static bst_status_t check_io(bst_plan_t p, const float* sino, int slices, const float* vol) {
+    if (!p || !sino || !vol || slices <= 0) return BST_ERR_INVALID_ARGUMENT;
+    const size_t ns = (size_t)slices * p->V * p->N * sizeof(float);
+    const size_t nv = (size_t)slices * p->N * p->N * sizeof(float);
+    if (ranges_overlap(sino, ns, vol, nv)) return BST_ERR_INVALID_ARGUMENT;
+    return BST_OK;
+}
+
+bst_status_t bst_fbp(bst_plan_t p, const float* d_sino, int slices, const float* d_g, float* d_volume, void* d_ws,
+                     size_t ws_bytes, bst_stream_t stream) {
+    bst_status_t s = check_io(p, d_sino, slices, d_volume);
+    if (s != BST_OK) return s;
+    const size_t need = bst_workspace_bytes(p, slices);
+    if (!d_ws || ws_bytes < need) return BST_ERR_WORKSPACE_TOO_SMALL;
+    return bst_launch_forward(p, d_sino, slices, BSTK_FILTER, d_g, d_volume, d_ws, ws_bytes, (cudaStream_t)stream);
+}
+
+bst_status_t bst_backproject(bst_plan_t p, const float* d_sino, int slices, float* d_volume, void* d_ws,
+                             size_t ws_bytes, bst_stream_t stream) {
+    bst_status_t s = check_io(p, d_sino, slices, d_volume);
+    if (s != BST_OK) return s;
+    const size_t need = bst_workspace_bytes(p, slices);
+    if (!d_ws || ws_bytes < need) return BST_ERR_WORKSPACE_TOO_SMALL;
+    return bst_launch_forward(p, d_sino, slices, BSTK_BACKPROJECT, nullptr, d_volume, d_ws, ws_bytes,
+                              (cudaStream_t)stream);
+}
+
+bst_status_t radon_adjoint(bst_plan_t p, bst_mode_t mode, const float* d_g, const float* d_volume, int slices,
+                           float* d_sino, void* d_ws, size_t ws_bytes, bst_stream_t stream) {
+    bst_status_t s = check_io(p, d_sino, slices, d_volume);
+    if (s != BST_OK) return s;
+    if (mode != BST_W_FILTER && mode != BST_W_BACKPROJECT) return BST_ERR_INVALID_ARGUMENT;
+    const size_t need = bst_adjoint_ws(p, slices);
+    if (!d_ws || ws_bytes < need) return BST_ERR_WORKSPACE_TOO_SMALL;
+    return bst_launch_adjoint(p, mode == BST_W_FILTER ? BSTK_FILTER : BSTK_BACKPROJECT,
+                              mode == BST_W_FILTER ? d_g : nullptr, d_volume, slices, d_sino, d_ws, ws_bytes,
+                              (cudaStream_t)stream);
+}
+
+bst_status_t bst_fbp_filter_grad(bst_plan_t p, const float* d_sino, const float* d_grad_vol, int slices,
+                                 float* d_grad_g, void* d_ws, size_t ws_bytes, bst_stream_t stream) {
+    bst_status_t s = check_io(p, d_sino, slices, d_grad_vol);
+    if (s != BST_OK) return s;
+    if (!d_grad_g) return BST_ERR_INVALID_ARGUMENT;
+    const size_t need = bst_adjoint_ws(p, slices);
+    if (!d_ws || ws_bytes < need) return BST_ERR_WORKSPACE_TOO_SMALL;
+    return bst_launch_filter_grad(p, d_sino, d_grad_vol, slices, d_grad_g, d_ws, ws_bytes, (cudaStream_t)stream);
+}
+
+bst_status_t brute_backproject(bst_plan_t p, const float* d_sino, int slices, const float* d_g, float* d_volume,
+                               void* d_ws, size_t ws_bytes, bst_stream_t stream) {
+    bst_status_t s = check_io(p, d_sino, slices, d_volume);
+    if (s != BST_OK) return s;
+    const size_t need = bst_brute_ws(p, slices, d_g != nullptr);
+    if (need > 0 && (!d_ws || ws_bytes < need)) return BST_ERR_WORKSPACE_TOO_SMALL;
+    return bst_launch_brute(p, d_sino, slices, d_g, d_volume, d_ws, ws_bytes, (cudaStream_t)stream);
+}
+
+bst_status_t bst_plan_status(bst_plan_t p, bst_stream_t stream) {
+    if (!p) return BST_ERR_INVALID_ARGUMENT;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return BST_ERR_CUDA;
+    int code = 0;
+    if (cudaMemcpy(&code, p->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return BST_ERR_CUDA;
+    return (bst_status_t)code;
+}
+
+}  // extern "C"

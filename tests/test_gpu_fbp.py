@@ -1,0 +1,113 @@
+"""GPU parity of bst_fbp and bst_backproject against the FP64 oracle
+(relative L2 <= 1e-5, max-abs <= 1e-4 max|ref|), through the C-ABI."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import bst as ob
+from gpu_util import assert_parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bst():
+    import paper_1704_08364_gb300 as m
+    return m
+
+
+def _run(bst, sino, theta, alpha=2, mode="fbp", g=None):
+    plan = bst.Plan(sino.shape[-1], theta, alpha)
+    d = torch.from_numpy(np.ascontiguousarray(sino, dtype=np.float32)).cuda()
+    dg = None if g is None else torch.from_numpy(np.asarray(g, dtype=np.float32)).cuda()
+    out = plan.fbp(d, dg) if mode == "fbp" else plan.backproject(d)
+    plan.status()
+    return out.cpu().numpy()
+
+
+def _oracle(sino, theta, alpha=2, mode="fbp", g=None):
+    m = ob.FILTER if mode == "fbp" else ob.BACKPROJECT
+    gg = None if g is None else np.asarray(g, dtype=np.float32).astype(np.float64)
+    return np.stack([ob.bst(s.astype(np.float64), theta, alpha, m, gg) for s in sino])
+
+
+def test_single_256_head_phantom(bst):
+    """The single-slice workload: 256 angles x 256 rays, ten-ellipse phantom."""
+    theta, sino, _ = synth.workload_slices("single-256", [0])
+    for mode in ("fbp", "bp"):
+        got = _run(bst, sino, theta, 2, mode)
+        assert_parity(got, _oracle(sino, theta, 2, mode), what=f"single-256 {mode}")
+
+
+@pytest.mark.parametrize("N,V,alpha", [
+    (8, 8, 2), (16, 12, 2), (24, 20, 2), (32, 32, 1), (48, 40, 2), (64, 64, 2), (96, 70, 1),
+    (128, 100, 2), (192, 128, 2), (256, 256, 1), (384, 300, 2), (512, 96, 2)])
+def test_sizes_modes_and_odd_slices(bst, N, V, alpha):
+    """Every supported FFT length family (2^a and 3 * 2^a), both pad factors,
+    odd slice counts (last pair padded with zeros), V not a multiple of the
+    lines per block."""
+    rng = np.random.default_rng(N * 1000 + V)
+    theta = synth.uniform_angles(V)
+    S = 3
+    sino = np.stack([synth.ellipse_sinogram(synth.random_ellipses(rng), theta, N) for _ in range(S)])
+    sino = synth.poisson_log_noise(sino, rng).astype(np.float32)
+    for mode in ("fbp", "bp"):
+        got = _run(bst, sino, theta, alpha, mode)
+        assert_parity(got, _oracle(sino, theta, alpha, mode), what=f"N={N} V={V} a={alpha} {mode}")
+
+
+def test_nonuniform_angles_and_filter_taps(bst):
+    rng = np.random.default_rng(11)
+    N, V = 64, 57
+    theta = np.sort(rng.uniform(0.02, np.pi - 0.01, V)).astype(np.float32)
+    sino = rng.standard_normal((2, V, N)).astype(np.float32)
+    g = rng.uniform(0.2, 1.5, N).astype(np.float32)
+    got = _run(bst, sino, theta, 2, "fbp", g)
+    assert_parity(got, _oracle(sino, theta, 2, "fbp", g), what="nonuniform+taps")
+    got = _run(bst, sino, theta, 2, "bp")
+    assert_parity(got, _oracle(sino, theta, 2, "bp"), what="nonuniform bp")
+
+
+def test_random_noise_sinogram_is_within_bar(bst):
+    """White-noise input has the flattest spectrum: the hardest case for FP32."""
+    rng = np.random.default_rng(5)
+    N = V = 256
+    theta = synth.uniform_angles(V)
+    sino = rng.standard_normal((2, V, N)).astype(np.float32)
+    assert_parity(_run(bst, sino, theta), _oracle(sino, theta), what="noise 256")
+
+
+def test_volume_512_sampled_slices(bst):
+    """512 slices x 512 x 512 with Poisson noise: the whole volume on the GPU in
+    one call, sampled slices against the oracle."""
+    idx = [0, 1, 255, 510, 511]
+    theta, sub, _ = synth.workload_slices("volume-512", idx)
+    plan = bst.Plan(512, theta, 2)
+    d = torch.zeros((512, 512, 512), dtype=torch.float32, device="cuda")
+    d[idx] = torch.from_numpy(sub).cuda()
+    out = plan.fbp(d)
+    plan.status()
+    got = out[idx].cpu().numpy()
+    for n, s in enumerate(idx):
+        assert_parity(got[n], ob.fbp(sub[n].astype(np.float64), theta), what=f"volume-512 slice {s}")
+
+
+def test_volume_2048_sampled_slices(bst):
+    """The 2048 x 2048 x 2048 workload in the benchmark's launch configuration
+    (one slice pair per chunk, 1024 chunks): sampled slices, regenerated on the
+    host, against the oracle."""
+    free, _ = torch.cuda.mem_get_info()
+    if free < 72 * 2**30:
+        pytest.skip("needs ~70 GiB of free device memory")
+    idx = [0, 1, 2047]
+    theta, sub, _ = synth.workload_slices("volume-2048", idx)
+    plan = bst.Plan(2048, theta, 2)
+    d = torch.zeros((2048, 2048, 2048), dtype=torch.float32, device="cuda")
+    d[idx] = torch.from_numpy(sub).cuda()
+    out = plan.fbp(d)
+    plan.status()
+    got = out[idx].cpu().numpy()
+    del d, out
+    for n, s in enumerate(idx):
+        assert_parity(got[n], ob.fbp(sub[n].astype(np.float64), theta), what=f"volume-2048 slice {s}")
