@@ -138,6 +138,29 @@ bst_status_t brute_backproject(bst_plan_t plan, const float* d_sino, int slices,
                                const float* d_g, float* d_volume,
                                void* d_ws, size_t ws_bytes, bst_stream_t stream);
 
+/* BST filtered backprojection exactly as bst_fbp, for callers that cannot
+ * allocate device memory where they reconstruct (an external memory manager
+ * owns the device's memory, or a cudaMalloc/cudaFree, which may synchronise
+ * the device, is not acceptable in the calling loop).  The paper has no
+ * counterpart: this is a deployment variant of the same operator.
+ * The call allocates nothing: its scratch is a fixed 8 MiB device array
+ * inside the library (bst_noalloc_scratch_bytes()), present on every GPU
+ * that loads the library until the process exits.  Plans whose one-pair
+ * workspace, (V M + 4 ceil(N/4) M) * 8 bytes, exceeds it (for example
+ * N = V > 512 at pad factor 2) are rejected with WORKSPACE_TOO_SMALL.
+ * The first call on a device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls on a device share the one array, so calls that overlap on the
+ * GPU (different streams or host threads without ordering) race and corrupt
+ * each other's results; serialise them.  No scratch content carries over
+ * between calls (every byte read is written earlier in the same call).
+ * Other arguments and errors as bst_fbp. */
+bst_status_t bst_fbp_noalloc(bst_plan_t plan, const float* d_sino, int slices,
+                             const float* d_g, float* d_volume, bst_stream_t stream);
+
+/* Size in bytes of bst_fbp_noalloc's fixed scratch array. */
+size_t bst_noalloc_scratch_bytes(void);
+
 /* Synchronise `stream` and return the plan's sticky device error (BST_OK if
  * none, BST_ERR_CUDA if the stream reported an error). */
 bst_status_t bst_plan_status(bst_plan_t plan, bst_stream_t stream);

@@ -125,6 +125,22 @@ class Plan:
         """BST filtered backprojection of sino [S][V][N] -> [S][N][N]."""
         return self._forward(sino, g, out, FILTER)
 
+    def fbp_noalloc(self, sino, g=None, out=None):
+        """As fbp, through bst_fbp_noalloc: the library's fixed scratch array
+        instead of a workspace (the output tensor is still the caller's)."""
+        _need(sino, "sino")
+        if sino.dim() == 2:
+            sino = sino.unsqueeze(0)
+        S = sino.shape[0]
+        _need(sino, "sino", (S, self.V, self.rays))
+        if g is not None:
+            _need(g, "g", (self.M // 2,))
+        if out is None:
+            out = torch.empty((S, self.rays, self.rays), dtype=torch.float32, device=sino.device)
+        _need(out, "out", (S, self.rays, self.rays))
+        _check(self._lib.bst_fbp_noalloc(self._h, _ptr(sino), S, _ptr(g), _ptr(out), _stream()), "bst_fbp_noalloc")
+        return out
+
     def backproject(self, sino, out=None):
         """Plain BST backprojection (1/sigma weight, zero DC)."""
         return self._forward(sino, None, out, BACKPROJECT)

@@ -77,6 +77,9 @@ void bst_timing_mark(bst_plan_s* p, cudaStream_t st, int stage);
 // launchers (one dispatch on M each), defined in the kernel translation units
 bst_status_t bst_launch_forward(bst_plan_s* p, const float* sino, int slices, int mode, const float* g,
                                 float* vol, void* ws, size_t ws_bytes, cudaStream_t st);
+// as bst_launch_forward, with at most max_chunk slice pairs per chunk of the workspace
+bst_status_t bst_launch_forward_chunked(bst_plan_s* p, const float* sino, int slices, int mode, const float* g,
+                                        float* vol, void* ws, cudaStream_t st, int max_chunk);
 bst_status_t bst_launch_adjoint(bst_plan_s* p, int mode, const float* g, const float* vol, int slices,
                                 float* sino, void* ws, size_t ws_bytes, cudaStream_t st);
 bst_status_t bst_launch_filter_grad(bst_plan_s* p, const float* sino, const float* gvol, int slices,

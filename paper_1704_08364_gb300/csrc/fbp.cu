@@ -251,7 +251,7 @@ template <int M> struct FwdCfg {
 
 template <int M>
 bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int mode, const float* g, float* vol,
-                              void* ws, cudaStream_t st) {
+                              void* ws, cudaStream_t st, int max_chunk) {
     using C = FwdCfg<M>;
     static bool attr_ok = set_smem(k_ray_fft<M, C::TPL, C::LPC1>, C::S1) &&
                           set_smem(k_grid_col<M, C::TPL, C::CPC>, C::S2) &&
@@ -259,7 +259,7 @@ bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int 
     if (!attr_ok) return BST_ERR_CUDA;
     const int N = p->N, V = p->V;
     const int pairs = (slices + 1) / 2;
-    const int chunk = std::min(pairs, p->chunk_pairs);
+    const int chunk = std::min(pairs, max_chunk);
     float2* Z = (float2*)ws;
     float2* T = Z + (size_t)chunk * V * M;
     const float scale = (float)((double)N / (2.0 * (double)M * (double)M));
@@ -287,15 +287,20 @@ bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int 
 #define BST_FOR_EACH_M(X) \
     X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(48) X(96) X(192) X(384) X(768) X(1536) X(3072)
 
-bst_status_t bst_launch_forward(bst_plan_s* p, const float* sino, int slices, int mode, const float* g, float* vol,
-                                void* ws, size_t /*ws_bytes*/, cudaStream_t st) {
+bst_status_t bst_launch_forward_chunked(bst_plan_s* p, const float* sino, int slices, int mode, const float* g,
+                                        float* vol, void* ws, cudaStream_t st, int max_chunk) {
     switch (p->M) {
 #define BST_CASE(m) \
-    case m: return bst::launch_forward_M<m>(p, sino, slices, mode, g, vol, ws, st);
+    case m: return bst::launch_forward_M<m>(p, sino, slices, mode, g, vol, ws, st, max_chunk);
         BST_FOR_EACH_M(BST_CASE)
 #undef BST_CASE
     }
     return BST_ERR_UNSUPPORTED_SIZE;
+}
+
+bst_status_t bst_launch_forward(bst_plan_s* p, const float* sino, int slices, int mode, const float* g, float* vol,
+                                void* ws, size_t /*ws_bytes*/, cudaStream_t st) {
+    return bst_launch_forward_chunked(p, sino, slices, mode, g, vol, ws, st, p->chunk_pairs);
 }
 
 namespace bst {
