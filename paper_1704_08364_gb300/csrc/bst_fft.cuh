@@ -153,6 +153,43 @@ struct SmemLine {
 
 // ---- passes ----------------------------------------------------------------
 
+// w[s] = tw[s * b] for s = 1..R-1 (b = k M / (NS R)): the powers of two of the
+// base root come from the table, the others are products of at most three
+// table values (error a few ulp), which quarters the table loads of a pass.
+template <int R>
+__device__ __forceinline__ void twiddles(const float2* __restrict__ tw, int b, float2* w) {
+    if constexpr (R == 2) {
+        w[1] = __ldg(tw + b);
+    } else if constexpr (R == 3) {
+        w[1] = __ldg(tw + b);
+        w[2] = __ldg(tw + 2 * b);
+    } else if constexpr (R == 4) {
+        w[1] = __ldg(tw + b);
+        w[2] = __ldg(tw + 2 * b);
+        w[3] = cmul(w[1], w[2]);
+    } else if constexpr (R == 8) {
+        w[1] = __ldg(tw + b);
+        w[2] = __ldg(tw + 2 * b);
+        w[4] = __ldg(tw + 4 * b);
+        w[3] = cmul(w[1], w[2]);
+        w[5] = cmul(w[1], w[4]);
+        w[6] = cmul(w[2], w[4]);
+        w[7] = cmul(w[3], w[4]);
+    } else {
+        static_assert(R == 16, "radix");
+        w[1] = __ldg(tw + b);
+        w[2] = __ldg(tw + 2 * b);
+        w[4] = __ldg(tw + 4 * b);
+        w[8] = __ldg(tw + 8 * b);
+        w[3] = cmul(w[1], w[2]);
+        w[5] = cmul(w[1], w[4]);
+        w[6] = cmul(w[2], w[4]);
+        w[7] = cmul(w[3], w[4]);
+#pragma unroll
+        for (int s = 1; s < 8; ++s) w[8 + s] = cmul(w[s], w[8]);
+    }
+}
+
 template <int M, int R, int NS, int TPL, bool INV, class Src, class Dst>
 __device__ __forceinline__ void stockham_pass(int t, const Src& src, const Dst& dst,
                                               const float2* __restrict__ tw, bool sync_mid) {
@@ -175,11 +212,10 @@ __device__ __forceinline__ void stockham_pass(int t, const Src& src, const Dst& 
             const int k = (NS == 1) ? 0 : (j % NS);
             if (NS > 1) {
                 constexpr int STEP = M / (NS * R);
+                float2 w[R];
+                twiddles<R>(tw, k * STEP, w);
 #pragma unroll
-                for (int s = 1; s < R; ++s) {
-                    const float2 w = __ldg(tw + k * s * STEP);
-                    a[it][s] = INV ? cmulc(a[it][s], w) : cmul(a[it][s], w);
-                }
+                for (int s = 1; s < R; ++s) a[it][s] = INV ? cmulc(a[it][s], w[s]) : cmul(a[it][s], w[s]);
             }
             Dft<R, INV>::run(a[it]);
             const int base = (j / NS) * NS * R + k;

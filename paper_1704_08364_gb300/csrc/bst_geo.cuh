@@ -29,6 +29,8 @@ struct Geo {
     const int* __restrict__ lut;       // [L] largest J with theta_J <= b pi / L (or -1)
     int V, M, L;
     float lut_scale;                   // L / pi
+    int uniform;                       // angles evenly spaced: bracket estimate by arithmetic
+    float th0, inv_step;               // theta_0 and 1 / spacing (uniform estimate only)
 };
 
 struct Polar {
@@ -50,28 +52,55 @@ __device__ __forceinline__ float cross_df(float4 d, float ux, float uy) {
     return __fadd_rn(__fsub_rn(p1, p2), lo);
 }
 
-// Polar coordinates of the Cartesian point (cx, ry), origin excluded.
-// Returns false when rho >= M/2 (the point is zero).
-__device__ __forceinline__ bool polar_of(int cx, int ry, const Geo& g, Polar& P) {
+// Angle of (ux, uy), uy >= 0, to within ~5e-6 rad: an odd polynomial of
+// degree 11 in the octant ratio (coefficients fitted by weighted least
+// squares to atan on [0, 1]).  Only an estimate: the bracket it selects is
+// verified with exact cross products.
+__device__ __forceinline__ float angle_estimate(float ux, float uy) {
+    const float ax = fabsf(ux);
+    const float mn = fminf(ax, uy), mx = fmaxf(ax, uy);
+    const float t = __fdividef(mn, mx);
+    const float t2 = t * t;
+    float p = fmaf(t2, -0.01017310842871666f, 0.04828116297721863f);
+    p = fmaf(t2, p, -0.11188798397779465f);
+    p = fmaf(t2, p, 0.19143280386924744f);
+    p = fmaf(t2, p, -0.33220672607421875f);
+    p = fmaf(t2, p, 0.9999518394470215f);
+    float a = t * p;
+    if (uy > ax) a = 1.57079632679489662f - a;
+    if (ux < 0.f) a = 3.14159265358979324f - a;
+    return a;
+}
+
+// Radial part of the polar coordinates of (cx, ry): rho = sqrt(cx^2 + ry^2)
+// as k0 = floor(rho) and frac = rho - k0 (from the exact integer rho^2), and
+// the sign of kappa.  Returns false when rho >= M/2 (the point is zero).
+__device__ __forceinline__ bool polar_radius(int cx, int ry, int M, Polar& P) {
     const int rho2 = cx * cx + ry * ry;
-    const int half = g.M >> 1;
+    const int half = M >> 1;
     if (rho2 >= half * half) return false;
-    const bool up = (ry > 0) || (ry == 0 && cx >= 0);
-    const float ux = (float)(up ? cx : -cx);
-    const float uy = (float)(up ? ry : -ry);
-    // radius: rho2 < 2^24 is exact in float
-    const float rf = __fsqrt_rn((float)rho2);
+    P.up = (ry > 0) || (ry == 0 && cx >= 0);
+    const float rf = __fsqrt_rn((float)rho2);   // rho2 < 2^24 is exact in float
     int k0 = (int)rf;
     if (k0 * k0 > rho2) --k0;
     else if ((k0 + 1) * (k0 + 1) <= rho2) ++k0;
-    P.frac = __fdiv_rn((float)(rho2 - k0 * k0), rf + (float)k0);
+    P.frac = __fdividef((float)(rho2 - k0 * k0), rf + (float)k0);
     P.k0 = k0;
-    P.up = up;
-    // angle bracket: table estimate, then exact sign tests against the neighbours
-    const float th = atan2f(uy, ux);
-    int b = (int)(th * g.lut_scale);
-    b = b < 0 ? 0 : (b >= g.L ? g.L - 1 : b);
-    int J = __ldg(g.lut + b);
+    return true;
+}
+
+// Angular part: bracket J and fraction fth of the direction (ux, uy), uy >= 0.
+__device__ __forceinline__ void polar_angle(float ux, float uy, const Geo& g, Polar& P) {
+    const float th = angle_estimate(ux, uy);
+    int J;
+    if (g.uniform) {
+        J = __float2int_rd((th - g.th0) * g.inv_step);
+    } else {
+        int b = (int)(th * g.lut_scale);
+        b = b < 0 ? 0 : (b >= g.L ? g.L - 1 : b);
+        J = __ldg(g.lut + b);
+    }
+    J = J < -1 ? -1 : (J > g.V - 1 ? g.V - 1 : J);
     while (J < g.V - 1 && cross_df(__ldg(g.dir + J + 2), ux, uy) >= 0.f) ++J;
     float4 d = __ldg(g.dir + J + 1);
     float cr = cross_df(d, ux, uy);
@@ -84,15 +113,24 @@ __device__ __forceinline__ bool polar_of(int cx, int ry, const Geo& g, Polar& P)
     float delta;
     if (fabsf(cr) <= 0.0625f * dt) {
         // atan(q) = q (1 - q^2/3 + q^4/5 - q^6/7), truncation < 1e-10 relative for |q| <= 1/16
-        const float q = __fdiv_rn(cr, dt);
+        const float q = __fdividef(cr, dt);
         const float q2 = q * q;
         delta = q * fmaf(q2, fmaf(q2, fmaf(q2, -1.0f / 7.0f, 0.2f), -1.0f / 3.0f), 1.0f);
     } else {
         delta = atan2f(cr, dt);
     }
-    float f = delta * __ldg(g.invdth + J + 1);
+    const float f = delta * __ldg(g.invdth + J + 1);
     P.fth = fminf(fmaxf(f, 0.f), 1.f);
     P.J = J;
+}
+
+// Polar coordinates of the Cartesian point (cx, ry), origin excluded.
+// Returns false when rho >= M/2 (the point is zero).
+__device__ __forceinline__ bool polar_of(int cx, int ry, const Geo& g, Polar& P) {
+    if (!polar_radius(cx, ry, g.M, P)) return false;
+    const float ux = (float)(P.up ? cx : -cx);
+    const float uy = (float)(P.up ? ry : -ry);
+    polar_angle(ux, uy, g, P);
     return true;
 }
 

@@ -19,10 +19,16 @@ struct bst_plan_s {
     int* lut = nullptr;             // [L]
     int L = 0;
     float lut_scale = 0.f;
+    int uniform = 0;                // evenly spaced angles (bracket estimate by arithmetic)
+    float th0 = 0.f, inv_step = 0.f;
     double2* cs64 = nullptr;        // [V] (cos, sin) in double, slant-stack tile origins
     float2* cs32 = nullptr;         // [V] (cos, sin) in float, slant-stack tile offsets
     float* wq = nullptr;            // [V] trapezoid weights of Eq. 2
     int* err = nullptr;             // sticky device error word
+    // angular part of the gridding geometry of the half grid c' in [0, M/2):
+    // bracket J (-2: point is zero) and fraction, [M/2][M], built at plan creation
+    short* geo_J = nullptr;
+    float* geo_f = nullptr;
     int chunk_pairs = 1;            // slice pairs per chunk of the forward path
     // gridding cell lists for the adjoint, built on first use
     int* cell_start = nullptr;      // [(V+1) M + 1]
@@ -47,6 +53,9 @@ struct bst_plan_s {
         g.M = M;
         g.L = L;
         g.lut_scale = lut_scale;
+        g.uniform = uniform;
+        g.th0 = th0;
+        g.inv_step = inv_step;
         return g;
     }
 };
@@ -87,6 +96,7 @@ bst_status_t bst_launch_filter_grad(bst_plan_s* p, const float* sino, const floa
 bst_status_t bst_launch_brute(bst_plan_s* p, const float* sino, int slices, const float* g, float* vol,
                               void* ws, size_t ws_bytes, cudaStream_t st);
 bst_status_t bst_build_cells(bst_plan_s* p, cudaStream_t st);
+bst_status_t bst_build_geo_table(bst_plan_s* p);
 size_t bst_adjoint_ws(const bst_plan_s* p, int slices);
 size_t bst_brute_ws(const bst_plan_s* p, int slices, int filtered);
 

@@ -104,28 +104,55 @@ struct ColDst {
     }
 };
 
+// Plan set-up: the angular part of the geometry of every point (q, r') of the
+// half grid q in [0, M/2) (the mirror half shares it), bracket -2 for points
+// that are zero (outside the band, or the origin, which takes the DC mean).
+__global__ void k_geo_table(Geo geo, int M, short* __restrict__ gJ, float* __restrict__ gF) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)(M / 2) * M) return;
+    const int q = (int)(idx / M), ridx = (int)(idx % M);
+    const int ry = signed_freq(ridx, M);
+    Polar P;
+    short J = -2;
+    float f = 0.f;
+    if (!(q == 0 && ry == 0) && polar_of(q, ry, geo, P)) {
+        J = (short)P.J;
+        f = P.fth;
+    }
+    gJ[idx] = J;
+    gF[idx] = f;
+}
+
 template <int M, int TPL, int CPC>
-__global__ void __launch_bounds__(2 * TPL * CPC)
-    k_grid_col(const float2* __restrict__ Z, int V, int N, Geo geo, float2* __restrict__ T,
-               const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(TPL * CPC, (TPL * CPC <= 256) ? 768 / (TPL * CPC) : 1)
+    k_grid_col(const float2* __restrict__ Z, int V, int N, const short* __restrict__ gJ,
+               const float* __restrict__ gF, float2* __restrict__ T, const float2* __restrict__ tw) {
     extern __shared__ float2 smem[];
+    constexpr int PPT = M / TPL;   // Cartesian points per thread and column
     const int pl = blockIdx.y;
     const float2* Zp = Z + (size_t)pl * V * M;
     float2* Tp = T + (size_t)pl * ((N + 3) / 4) * 4 * M;
-    const int cp = threadIdx.x / (2 * TPL);
-    const int lt = threadIdx.x % (2 * TPL);
+    const int cp = threadIdx.x / TPL;
+    const int t = threadIdx.x % TPL;
     const int q = blockIdx.x * CPC + cp;
     const bool live = q < (M >> 1);
     const SmemLine smA{smem + (2 * cp) * smem_line_len(M)};
     const SmemLine smB{smem + (2 * cp + 1) * smem_line_len(M)};
     // P0 + P5: polar coordinates once per point, taps for (q, r') and (-q, -r');
-    // the mirror column is stored index-reversed (its transform is read back reversed)
-    for (int ridx = lt; ridx < M; ridx += 2 * TPL) {
+    // the mirror column is stored index-reversed (its transform is read back
+    // reversed).  Consecutive lanes take consecutive rows, so a warp's taps
+    // fall on neighbouring polar samples.
+    for (int i = 0; i < PPT; ++i) {
+        const int ridx = t + i * TPL;
         float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
         if (live) {
             const int ry = signed_freq(ridx, M);
+            const int Jt = __ldcs(gJ + (size_t)q * M + ridx);
+            const float ft = __ldcs(gF + (size_t)q * M + ridx);
             Polar P;
-            if (!(q == 0 && ry == 0) && polar_of(q, ry, geo, P)) {
+            if (Jt >= -1 && polar_radius(q, ry, M, P)) {
+                P.J = Jt;
+                P.fth = ft;
                 int K0;
                 float fk;
                 radial_bin(P, P.up, K0, fk);
@@ -141,10 +168,10 @@ __global__ void __launch_bounds__(2 * TPL * CPC)
     }
     // the origin is single-valued: mean over angles of the DC bin
     if (live && q == 0) {
-        if constexpr (2 * TPL >= 32) {
-            if (lt < 32) {
+        if constexpr (TPL >= 32) {
+            if (t < 32) {
                 float sx = 0.f, sy = 0.f;
-                for (int j = lt; j < V; j += 32) {
+                for (int j = t; j < V; j += 32) {
                     const float2 z = __ldg(Zp + (size_t)j * M);
                     sx += z.x;
                     sy += z.y;
@@ -154,10 +181,10 @@ __global__ void __launch_bounds__(2 * TPL * CPC)
                     sx += __shfl_xor_sync(0xffffffffu, sx, o);
                     sy += __shfl_xor_sync(0xffffffffu, sy, o);
                 }
-                if (lt == 0) smA.store(0, make_float2(sx / (float)V, sy / (float)V));
+                if (t == 0) smA.store(0, make_float2(sx / (float)V, sy / (float)V));
             }
         } else {
-            if (lt == 0) {
+            if (t == 0) {
                 float sx = 0.f, sy = 0.f;
                 for (int j = 0; j < V; ++j) {
                     const float2 z = __ldg(Zp + (size_t)j * M);
@@ -169,12 +196,11 @@ __global__ void __launch_bounds__(2 * TPL * CPC)
         }
     }
     __syncthreads();
-    const int half = lt / TPL;
-    const int t = lt % TPL;
-    const SmemLine sm = half ? smB : smA;
-    const int cidx = half ? (q == 0 ? (M >> 1) : M - q) : q;
-    ColDst dst{Tp, N, M, cidx, half != 0 && q != 0, live};
-    fft_line<M, TPL, true>(t, sm, dst, sm, tw);
+    // column q, then its mirror -q, each by the same TPL threads
+    const ColDst dstA{Tp, N, M, q, false, live};
+    fft_line<M, TPL, true>(t, smA, dstA, smA, tw);
+    const ColDst dstB{Tp, N, M, q == 0 ? (M >> 1) : M - q, q != 0, live};
+    fft_line<M, TPL, true>(t, smB, dstB, smB, tw);
 }
 
 // ---------------------------------------------------------------------------
@@ -242,7 +268,7 @@ static bool set_smem(K kernel, size_t bytes) {
 template <int M> struct FwdCfg {
     static constexpr int TPL = tpl_of<M>();
     static constexpr int LPC1 = (256 / TPL) > 1 ? 256 / TPL : 1;
-    static constexpr int CPC = (128 / (2 * TPL)) > 1 ? 128 / (2 * TPL) : 1;
+    static constexpr int CPC = (128 / TPL) > 1 ? 128 / TPL : 1;
     static constexpr int TPC = (128 / (4 * TPL)) > 1 ? 128 / (4 * TPL) : 1;
     static constexpr size_t S1 = (size_t)LPC1 * smem_line_len(M) * sizeof(float2);
     static constexpr size_t S2 = (size_t)2 * CPC * smem_line_len(M) * sizeof(float2);
@@ -264,7 +290,6 @@ bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int 
     float2* T = Z + (size_t)chunk * V * M;
     const float scale = (float)((double)N / (2.0 * (double)M * (double)M));
     const float two_alpha = (float)(2 * p->alpha);
-    const bst::Geo geo = p->geo();
     const int row_tiles = (N + 3) / 4;
     for (int p0 = 0; p0 < pairs; p0 += chunk) {
         const int np = std::min(chunk, pairs - p0);
@@ -272,8 +297,8 @@ bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int 
         k_ray_fft<M, C::TPL, C::LPC1><<<dim3((V + C::LPC1 - 1) / C::LPC1, np), C::TPL * C::LPC1, C::S1, st>>>(
             sino, slices, p0, N, V, mode, g, two_alpha, Z, p->tw);
         bst_timing_mark(p, st, 0);
-        k_grid_col<M, C::TPL, C::CPC><<<dim3((M / 2 + C::CPC - 1) / C::CPC, np), 2 * C::TPL * C::CPC, C::S2, st>>>(
-            Z, V, N, geo, T, p->tw);
+        k_grid_col<M, C::TPL, C::CPC><<<dim3((M / 2 + C::CPC - 1) / C::CPC, np), C::TPL * C::CPC, C::S2, st>>>(
+            Z, V, N, p->geo_J, p->geo_f, T, p->tw);
         bst_timing_mark(p, st, 1);
         k_row_ifft<M, C::TPL, C::TPC><<<dim3((row_tiles + C::TPC - 1) / C::TPC, np), 4 * C::TPL * C::TPC, C::S3, st>>>(
             T, slices, p0, N, scale, vol, p->tw);
@@ -328,4 +353,13 @@ bst_status_t bst_launch_ray_spectrum(bst_plan_s* p, const float* sino, int slice
 #undef BST_CASE
     }
     return BST_ERR_UNSUPPORTED_SIZE;
+}
+
+bst_status_t bst_build_geo_table(bst_plan_s* p) {
+    const size_t n = (size_t)(p->M / 2) * p->M;
+    if (cudaMalloc((void**)&p->geo_J, n * sizeof(short)) != cudaSuccess) return BST_ERR_OUT_OF_MEMORY;
+    if (cudaMalloc((void**)&p->geo_f, n * sizeof(float)) != cudaSuccess) return BST_ERR_OUT_OF_MEMORY;
+    bst::k_geo_table<<<(unsigned)((n + 255) / 256), 256>>>(p->geo(), p->M, p->geo_J, p->geo_f);
+    if (cudaGetLastError() != cudaSuccess) return BST_ERR_CUDA;
+    return cudaDeviceSynchronize() == cudaSuccess ? BST_OK : BST_ERR_CUDA;
 }

@@ -35,6 +35,8 @@ void free_plan(bst_plan_s* p) {
     cudaFree(p->cell_start);
     cudaFree(p->cell_pts);
     cudaFree(p->cell_w);
+    cudaFree(p->geo_J);
+    cudaFree(p->geo_f);
     delete p;
 }
 
@@ -170,6 +172,16 @@ bst_status_t bst_plan_create(bst_plan_t* out, int rays, int angles, const float*
     }
     p->L = L;
     p->lut_scale = (float)((double)L / M_PI);
+    {
+        // evenly spaced angles: the gridding estimates the bracket arithmetically
+        // (the estimate only saves a table lookup; exact tests decide the bracket)
+        const double step = (th[V - 1] - th[0]) / (double)(V - 1);
+        double dev = 0.0;
+        for (int j = 0; j < V; ++j) dev = std::max(dev, std::fabs(th[j] - (th[0] + j * step)));
+        p->uniform = (step > 0.0 && dev <= 1e-3 * step) ? 1 : 0;
+        p->th0 = (float)th[0];
+        p->inv_step = (float)(1.0 / step);
+    }
     bool ok = upload(&p->tw, tw) && upload(&p->dir, dir) && upload(&p->invdth, invdth) && upload(&p->lut, lut) &&
               upload(&p->cs64, cs64) && upload(&p->cs32, cs32) && upload(&p->wq, wq);
     if (ok) ok = cudaMalloc((void**)&p->err, sizeof(int)) == cudaSuccess && cudaMemset(p->err, 0, sizeof(int)) == cudaSuccess;
@@ -177,6 +189,14 @@ bst_status_t bst_plan_create(bst_plan_t* out, int rays, int angles, const float*
         cudaGetLastError();
         free_plan(p);
         return BST_ERR_OUT_OF_MEMORY;
+    }
+    {
+        const bst_status_t gs = bst_build_geo_table(p);
+        if (gs != BST_OK) {
+            cudaGetLastError();
+            free_plan(p);
+            return gs;
+        }
     }
     const size_t per_pair = bsth::fwd_bytes_per_pair(p);
     const size_t budget = (size_t)64 << 20;
