@@ -30,6 +30,11 @@ struct bst_plan_s {
     short* geo_J = nullptr;
     float* geo_f = nullptr;
     int chunk_pairs = 1;            // slice pairs per chunk of the forward path
+    // two plan-owned streams that alternate chunks of the forward path (fork
+    // from and join back to the caller's stream with events), created on first use
+    cudaStream_t lane[2] = {nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr;
+    cudaEvent_t ev_join[2] = {nullptr, nullptr};
     // gridding cell lists for the adjoint, built on first use
     int* cell_start = nullptr;      // [(V+1) M + 1]
     int* cell_pts = nullptr;        // [n] index c * M + r of each Cartesian point
@@ -71,7 +76,7 @@ inline bool supported_fft_length(int M) {
 
 inline bool check_cuda(cudaError_t e) { return e == cudaSuccess; }
 
-// byte sizes of the per-pair workspace of the forward path
+// byte sizes of the per-pair workspace of the forward path (one lane)
 inline size_t fwd_bytes_per_pair(const bst_plan_s* p) {
     const size_t rows_t = (size_t)((p->N + 3) / 4) * 4;
     return ((size_t)p->V * p->M + rows_t * p->M) * sizeof(float2);
@@ -86,9 +91,12 @@ void bst_timing_mark(bst_plan_s* p, cudaStream_t st, int stage);
 // launchers (one dispatch on M each), defined in the kernel translation units
 bst_status_t bst_launch_forward(bst_plan_s* p, const float* sino, int slices, int mode, const float* g,
                                 float* vol, void* ws, size_t ws_bytes, cudaStream_t st);
-// as bst_launch_forward, with at most max_chunk slice pairs per chunk of the workspace
+// as bst_launch_forward, with at most max_chunk slice pairs per chunk of the
+// workspace and up to `lanes` (1 or 2) streams alternating the chunks
 bst_status_t bst_launch_forward_chunked(bst_plan_s* p, const float* sino, int slices, int mode, const float* g,
-                                        float* vol, void* ws, cudaStream_t st, int max_chunk);
+                                        float* vol, void* ws, cudaStream_t st, int max_chunk, int lanes);
+// create the plan's two chunk streams and their events (false on failure)
+bool bst_ensure_lanes(bst_plan_s* p);
 bst_status_t bst_launch_adjoint(bst_plan_s* p, int mode, const float* g, const float* vol, int slices,
                                 float* sino, void* ws, size_t ws_bytes, cudaStream_t st);
 bst_status_t bst_launch_filter_grad(bst_plan_s* p, const float* sino, const float* gvol, int slices,

@@ -123,12 +123,63 @@ __global__ void k_geo_table(Geo geo, int M, short* __restrict__ gJ, float* __res
     gF[idx] = f;
 }
 
+// Bilinear gather of one side of a column pair: plus = true for the point
+// (q, r') itself (kappa = +rho when P.up), false for its mirror (-q, -r').
+// Two points per step; all eight tap loads are issued before any is used.
+template <int M, int TPL, int PPT>
+__device__ __forceinline__ void gather_side(const float2* __restrict__ Zp, int V, int q, bool live, int t,
+                                            const short* __restrict__ gJq, const float* __restrict__ gFq,
+                                            bool mirror, const SmemLine& sm) {
+#pragma unroll 1
+    for (int i = 0; i < PPT; i += 2) {
+        float2 z[2][4];
+        float wk[2], wt[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int ridx = t + (i + u) * TPL;
+            const int ry = signed_freq(ridx, M);
+            const int Jt = __ldg(gJq + ridx);
+            wt[u] = __ldg(gFq + ridx);
+            Polar P{0, 0.f, 0, 0.f, true};
+            const bool ok = live && Jt >= -1 && polar_radius(q, ry, M, P);
+            const int J = ok ? Jt : 0;
+            int K0;
+            radial_bin(P, mirror ? !P.up : P.up, K0, wk[u]);
+            // rows of the bracket; virtual rows -1 and V read rows V-1 and 0 at -k
+            const int rowA = J < 0 ? V - 1 : J;
+            const int sA = J < 0 ? -1 : 1;
+            const int rowB = J + 1 >= V ? 0 : J + 1;
+            const int sB = J + 1 >= V ? -1 : 1;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int bA = sA * (K0 + c), bB = sB * (K0 + c);
+                const bool vA = ok && bA < (M >> 1) && bA > -(M >> 1);
+                const bool vB = ok && bB < (M >> 1) && bB > -(M >> 1);
+                const size_t oA = vA ? (size_t)rowA * M + (bA < 0 ? bA + M : bA) : 0;
+                const size_t oB = vB ? (size_t)rowB * M + (bB < 0 ? bB + M : bB) : 0;
+                const float2 za = __ldg(Zp + oA), zb = __ldg(Zp + oB);
+                z[u][c] = vA ? za : make_float2(0.f, 0.f);
+                z[u][2 + c] = vB ? zb : make_float2(0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float fk = wk[u], ft = wt[u];
+            const float2 z00 = z[u][0], z01 = z[u][1], z10 = z[u][2], z11 = z[u][3];
+            const float2 a = make_float2(fmaf(fk, z01.x - z00.x, z00.x), fmaf(fk, z01.y - z00.y, z00.y));
+            const float2 b = make_float2(fmaf(fk, z11.x - z10.x, z10.x), fmaf(fk, z11.y - z10.y, z10.y));
+            sm.store(t + (i + u) * TPL, make_float2(fmaf(ft, b.x - a.x, a.x), fmaf(ft, b.y - a.y, a.y)));
+        }
+    }
+}
+
 template <int M, int TPL, int CPC>
-__global__ void __launch_bounds__(TPL * CPC, (TPL * CPC <= 256) ? 768 / (TPL * CPC) : 1)
+__global__ void __launch_bounds__(TPL * CPC, (TPL * CPC <= 256) ? 1024 / (TPL * CPC) : 1)
     k_grid_col(const float2* __restrict__ Z, int V, int N, const short* __restrict__ gJ,
                const float* __restrict__ gF, float2* __restrict__ T, const float2* __restrict__ tw) {
     extern __shared__ float2 smem[];
     constexpr int PPT = M / TPL;   // Cartesian points per thread and column
+    static_assert(PPT % 2 == 0, "points per thread");
     const int pl = blockIdx.y;
     const float2* Zp = Z + (size_t)pl * V * M;
     float2* Tp = T + (size_t)pl * ((N + 3) / 4) * 4 * M;
@@ -136,71 +187,55 @@ __global__ void __launch_bounds__(TPL * CPC, (TPL * CPC <= 256) ? 768 / (TPL * C
     const int t = threadIdx.x % TPL;
     const int q = blockIdx.x * CPC + cp;
     const bool live = q < (M >> 1);
-    const SmemLine smA{smem + (2 * cp) * smem_line_len(M)};
-    const SmemLine smB{smem + (2 * cp + 1) * smem_line_len(M)};
-    // P0 + P5: polar coordinates once per point, taps for (q, r') and (-q, -r');
-    // the mirror column is stored index-reversed (its transform is read back
-    // reversed).  Consecutive lanes take consecutive rows, so a warp's taps
-    // fall on neighbouring polar samples.
-    for (int i = 0; i < PPT; ++i) {
-        const int ridx = t + i * TPL;
-        float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
-        if (live) {
-            const int ry = signed_freq(ridx, M);
-            const int Jt = __ldcs(gJ + (size_t)q * M + ridx);
-            const float ft = __ldcs(gF + (size_t)q * M + ridx);
-            Polar P;
-            if (Jt >= -1 && polar_radius(q, ry, M, P)) {
-                P.J = Jt;
-                P.fth = ft;
-                int K0;
-                float fk;
-                radial_bin(P, P.up, K0, fk);
-                va = polar_gather(Zp, V, M, P.J, P.fth, K0, fk);
-                if (q != 0) {
-                    radial_bin(P, !P.up, K0, fk);
-                    vb = polar_gather(Zp, V, M, P.J, P.fth, K0, fk);
-                }
-            }
-        }
-        smA.store(ridx, va);
-        smB.store(ridx, vb);
-    }
-    // the origin is single-valued: mean over angles of the DC bin
-    if (live && q == 0) {
-        if constexpr (TPL >= 32) {
-            if (t < 32) {
-                float sx = 0.f, sy = 0.f;
-                for (int j = t; j < V; j += 32) {
-                    const float2 z = __ldg(Zp + (size_t)j * M);
-                    sx += z.x;
-                    sy += z.y;
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    sx += __shfl_xor_sync(0xffffffffu, sx, o);
-                    sy += __shfl_xor_sync(0xffffffffu, sy, o);
-                }
-                if (t == 0) smA.store(0, make_float2(sx / (float)V, sy / (float)V));
-            }
+    const SmemLine sm{smem + cp * smem_line_len(M)};
+    const short* gJq = gJ + (size_t)(live ? q : 0) * M;
+    const float* gFq = gF + (size_t)(live ? q : 0) * M;
+    // P0 + P5 then the column inverse FFT, first for column q, then for its
+    // mirror -q (the same angular geometry; stored index-reversed, its
+    // transform is read back reversed; column -M/2 pairs with q = 0 and is
+    // zero).  Consecutive lanes take consecutive rows, so a warp's taps fall
+    // on neighbouring polar samples.
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        if (side == 0 || q != 0) {
+            gather_side<M, TPL, PPT>(Zp, V, q, live, t, gJq, gFq, side == 1, sm);
         } else {
-            if (t == 0) {
-                float sx = 0.f, sy = 0.f;
-                for (int j = 0; j < V; ++j) {
-                    const float2 z = __ldg(Zp + (size_t)j * M);
-                    sx += z.x;
-                    sy += z.y;
+            for (int i = 0; i < PPT; ++i) sm.store(t + i * TPL, make_float2(0.f, 0.f));
+        }
+        // the origin is single-valued: mean over angles of the DC bin
+        if (side == 0 && live && q == 0) {
+            if constexpr (TPL >= 32) {
+                if (t < 32) {
+                    float sx = 0.f, sy = 0.f;
+                    for (int j = t; j < V; j += 32) {
+                        const float2 zz = __ldg(Zp + (size_t)j * M);
+                        sx += zz.x;
+                        sy += zz.y;
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                    }
+                    if (t == 0) sm.store(0, make_float2(sx / (float)V, sy / (float)V));
                 }
-                smA.store(0, make_float2(sx / (float)V, sy / (float)V));
+            } else {
+                if (t == 0) {
+                    float sx = 0.f, sy = 0.f;
+                    for (int j = 0; j < V; ++j) {
+                        const float2 zz = __ldg(Zp + (size_t)j * M);
+                        sx += zz.x;
+                        sy += zz.y;
+                    }
+                    sm.store(0, make_float2(sx / (float)V, sy / (float)V));
+                }
             }
         }
+        __syncthreads();
+        const ColDst dst{Tp, N, M, side == 0 ? q : (q == 0 ? (M >> 1) : M - q), side == 1 && q != 0, live};
+        fft_line<M, TPL, true>(t, sm, dst, sm, tw);
+        __syncthreads();
     }
-    __syncthreads();
-    // column q, then its mirror -q, each by the same TPL threads
-    const ColDst dstA{Tp, N, M, q, false, live};
-    fft_line<M, TPL, true>(t, smA, dstA, smA, tw);
-    const ColDst dstB{Tp, N, M, q == 0 ? (M >> 1) : M - q, q != 0, live};
-    fft_line<M, TPL, true>(t, smB, dstB, smB, tw);
 }
 
 // ---------------------------------------------------------------------------
@@ -271,13 +306,13 @@ template <int M> struct FwdCfg {
     static constexpr int CPC = (128 / TPL) > 1 ? 128 / TPL : 1;
     static constexpr int TPC = (128 / (4 * TPL)) > 1 ? 128 / (4 * TPL) : 1;
     static constexpr size_t S1 = (size_t)LPC1 * smem_line_len(M) * sizeof(float2);
-    static constexpr size_t S2 = (size_t)2 * CPC * smem_line_len(M) * sizeof(float2);
+    static constexpr size_t S2 = (size_t)CPC * smem_line_len(M) * sizeof(float2);
     static constexpr size_t S3 = (size_t)4 * TPC * row_line_stride<M>() * sizeof(float2);
 };
 
 template <int M>
 bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int mode, const float* g, float* vol,
-                              void* ws, cudaStream_t st, int max_chunk) {
+                              void* ws, cudaStream_t st, int max_chunk, int lanes) {
     using C = FwdCfg<M>;
     static bool attr_ok = set_smem(k_ray_fft<M, C::TPL, C::LPC1>, C::S1) &&
                           set_smem(k_grid_col<M, C::TPL, C::CPC>, C::S2) &&
@@ -286,23 +321,43 @@ bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int 
     const int N = p->N, V = p->V;
     const int pairs = (slices + 1) / 2;
     const int chunk = std::min(pairs, max_chunk);
-    float2* Z = (float2*)ws;
-    float2* T = Z + (size_t)chunk * V * M;
+    const int nchunks = (pairs + chunk - 1) / chunk;
+    // chunks alternate between two streams (each with its own half of the
+    // workspace) so that one chunk's gridding overlaps the next chunk's FFTs;
+    // per-stage timing keeps everything on the caller's stream
+    const int nl = (lanes >= 2 && nchunks >= 2 && !p->timing && bst_ensure_lanes(p)) ? 2 : 1;
+    const size_t lane_elems = (size_t)chunk * (V + (size_t)((N + 3) / 4) * 4) * M;
     const float scale = (float)((double)N / (2.0 * (double)M * (double)M));
     const float two_alpha = (float)(2 * p->alpha);
     const int row_tiles = (N + 3) / 4;
-    for (int p0 = 0; p0 < pairs; p0 += chunk) {
+    if (nl == 2) {
+        if (cudaEventRecord(p->ev_fork, st) != cudaSuccess) return BST_ERR_CUDA;
+        for (int l = 0; l < 2; ++l)
+            if (cudaStreamWaitEvent(p->lane[l], p->ev_fork, 0) != cudaSuccess) return BST_ERR_CUDA;
+    }
+    for (int c = 0; c < nchunks; ++c) {
+        const int p0 = c * chunk;
         const int np = std::min(chunk, pairs - p0);
-        bst_timing_mark(p, st, -1);
-        k_ray_fft<M, C::TPL, C::LPC1><<<dim3((V + C::LPC1 - 1) / C::LPC1, np), C::TPL * C::LPC1, C::S1, st>>>(
+        const int l = c % nl;
+        cudaStream_t s = nl == 2 ? p->lane[l] : st;
+        float2* Z = (float2*)ws + (size_t)l * lane_elems;
+        float2* T = Z + (size_t)chunk * V * M;
+        bst_timing_mark(p, s, -1);
+        k_ray_fft<M, C::TPL, C::LPC1><<<dim3((V + C::LPC1 - 1) / C::LPC1, np), C::TPL * C::LPC1, C::S1, s>>>(
             sino, slices, p0, N, V, mode, g, two_alpha, Z, p->tw);
-        bst_timing_mark(p, st, 0);
-        k_grid_col<M, C::TPL, C::CPC><<<dim3((M / 2 + C::CPC - 1) / C::CPC, np), C::TPL * C::CPC, C::S2, st>>>(
+        bst_timing_mark(p, s, 0);
+        k_grid_col<M, C::TPL, C::CPC><<<dim3((M / 2 + C::CPC - 1) / C::CPC, np), C::TPL * C::CPC, C::S2, s>>>(
             Z, V, N, p->geo_J, p->geo_f, T, p->tw);
-        bst_timing_mark(p, st, 1);
-        k_row_ifft<M, C::TPL, C::TPC><<<dim3((row_tiles + C::TPC - 1) / C::TPC, np), 4 * C::TPL * C::TPC, C::S3, st>>>(
+        bst_timing_mark(p, s, 1);
+        k_row_ifft<M, C::TPL, C::TPC><<<dim3((row_tiles + C::TPC - 1) / C::TPC, np), 4 * C::TPL * C::TPC, C::S3, s>>>(
             T, slices, p0, N, scale, vol, p->tw);
-        bst_timing_mark(p, st, 2);
+        bst_timing_mark(p, s, 2);
+    }
+    if (nl == 2) {
+        for (int l = 0; l < 2; ++l) {
+            if (cudaEventRecord(p->ev_join[l], p->lane[l]) != cudaSuccess) return BST_ERR_CUDA;
+            if (cudaStreamWaitEvent(st, p->ev_join[l], 0) != cudaSuccess) return BST_ERR_CUDA;
+        }
     }
     return cudaGetLastError() == cudaSuccess ? BST_OK : BST_ERR_CUDA;
 }
@@ -313,10 +368,10 @@ bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int 
     X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(48) X(96) X(192) X(384) X(768) X(1536) X(3072)
 
 bst_status_t bst_launch_forward_chunked(bst_plan_s* p, const float* sino, int slices, int mode, const float* g,
-                                        float* vol, void* ws, cudaStream_t st, int max_chunk) {
+                                        float* vol, void* ws, cudaStream_t st, int max_chunk, int lanes) {
     switch (p->M) {
 #define BST_CASE(m) \
-    case m: return bst::launch_forward_M<m>(p, sino, slices, mode, g, vol, ws, st, max_chunk);
+    case m: return bst::launch_forward_M<m>(p, sino, slices, mode, g, vol, ws, st, max_chunk, lanes);
         BST_FOR_EACH_M(BST_CASE)
 #undef BST_CASE
     }
@@ -324,8 +379,11 @@ bst_status_t bst_launch_forward_chunked(bst_plan_s* p, const float* sino, int sl
 }
 
 bst_status_t bst_launch_forward(bst_plan_s* p, const float* sino, int slices, int mode, const float* g, float* vol,
-                                void* ws, size_t /*ws_bytes*/, cudaStream_t st) {
-    return bst_launch_forward_chunked(p, sino, slices, mode, g, vol, ws, st, p->chunk_pairs);
+                                void* ws, size_t ws_bytes, cudaStream_t st) {
+    const int pairs = (slices + 1) / 2;
+    const int chunk = std::min(pairs, p->chunk_pairs);
+    const int lanes = ws_bytes >= 2 * (size_t)chunk * bsth::fwd_bytes_per_pair(p) ? 2 : 1;
+    return bst_launch_forward_chunked(p, sino, slices, mode, g, vol, ws, st, p->chunk_pairs, lanes);
 }
 
 namespace bst {

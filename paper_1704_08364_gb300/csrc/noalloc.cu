@@ -74,7 +74,7 @@ bst_status_t bst_fbp_noalloc(bst_plan_t p, const float* d_sino, int slices, cons
     // nothing needs clearing between calls
     const int max_chunk = (int)std::min<size_t>((size_t)p->chunk_pairs, BST_NOALLOC_SCRATCH_BYTES / per_pair);
     return bst_launch_forward_chunked(p, d_sino, slices, BSTK_FILTER, d_g, d_volume, ws, (cudaStream_t)stream,
-                                      max_chunk);
+                                      max_chunk, 1);
 }
 
 }  // extern "C"

@@ -24,6 +24,11 @@ bool upload(T** dptr, const std::vector<T>& host) {
 void free_plan(bst_plan_s* p) {
     if (!p) return;
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+    for (int i = 0; i < 2; ++i) {
+        if (p->lane[i]) cudaStreamDestroy(p->lane[i]);
+        if (p->ev_join[i]) cudaEventDestroy(p->ev_join[i]);
+    }
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     cudaFree(p->tw);
     cudaFree(p->dir);
     cudaFree(p->invdth);
@@ -51,6 +56,17 @@ bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
 }
 
 }  // namespace
+
+bool bst_ensure_lanes(bst_plan_s* p) {
+    if (p->lane[0] && p->lane[1]) return true;
+    for (int i = 0; i < 2; ++i) {
+        if (!p->lane[i] && cudaStreamCreateWithFlags(&p->lane[i], cudaStreamNonBlocking) != cudaSuccess) return false;
+        if (!p->ev_join[i] && cudaEventCreateWithFlags(&p->ev_join[i], cudaEventDisableTiming) != cudaSuccess)
+            return false;
+    }
+    if (!p->ev_fork && cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess) return false;
+    return true;
+}
 
 void bst_timing_mark(bst_plan_s* p, cudaStream_t st, int stage) {
     if (!p->timing) return;
@@ -217,7 +233,9 @@ int bst_plan_fft_length(bst_plan_t p) { return p ? p->M : 0; }
 size_t bst_workspace_bytes(bst_plan_t p, int slices) {
     if (!p || slices <= 0) return 0;
     const int pairs = (slices + 1) / 2;
-    return (size_t)std::min(pairs, p->chunk_pairs) * bsth::fwd_bytes_per_pair(p);
+    const int chunk = std::min(pairs, p->chunk_pairs);
+    const int lanes = pairs > chunk ? 2 : 1;   // two chunks in flight when there is more than one
+    return (size_t)lanes * chunk * bsth::fwd_bytes_per_pair(p);
 }
 
 size_t bst_adjoint_workspace_bytes(bst_plan_t p, int slices) {
