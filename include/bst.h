@@ -161,6 +161,24 @@ bst_status_t bst_fbp_noalloc(bst_plan_t plan, const float* d_sino, int slices,
 /* Size in bytes of bst_fbp_noalloc's fixed scratch array. */
 size_t bst_noalloc_scratch_bytes(void);
 
+/* Device workspace in bytes for bst_fbp_host: two staging buffers per
+ * direction for chunks of about 512 MiB of input, plus the forward workspace. */
+size_t bst_host_workspace_bytes(bst_plan_t plan, int slices);
+
+/* BST filtered backprojection of a volume in host memory:
+ *   h_sino    [slices][V][N] float32, host (page-locked for full overlap)
+ *   h_volume  [slices][N][N] float32, host
+ *   d_g       as bst_fbp (device memory or NULL)
+ *   d_ws      device workspace of bst_host_workspace_bytes(plan, slices)
+ * Chunks of slices are uploaded, reconstructed and downloaded with the copies
+ * of one chunk overlapping the computation of its neighbours (the overlap of
+ * data movement and GPU stages of Sec. 3), on `stream` and two plan-owned copy
+ * streams.  Asynchronous: the host buffers must stay valid until `stream`
+ * completes, which it does after the last download.  Errors as bst_fbp. */
+bst_status_t bst_fbp_host(bst_plan_t plan, const float* h_sino, int slices,
+                          const float* d_g, float* h_volume,
+                          void* d_ws, size_t ws_bytes, bst_stream_t stream);
+
 /* Synchronise `stream` and return the plan's sticky device error (BST_OK if
  * none, BST_ERR_CUDA if the stream reported an error). */
 bst_status_t bst_plan_status(bst_plan_t plan, bst_stream_t stream);

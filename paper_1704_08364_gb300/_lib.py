@@ -31,6 +31,8 @@ SIGNATURES = {
     "bst_status_string": (ctypes.c_char_p, [c_int]),
     "bst_plan_fft_length": (c_int, [c_plan]),
     "bst_fbp_noalloc": (c_int, [c_plan, c_ptr, c_int, c_ptr, c_ptr, c_ptr]),
+    "bst_host_workspace_bytes": (c_size, [c_plan, c_int]),
+    "bst_fbp_host": (c_int, [c_plan, c_ptr, c_int, c_ptr, c_ptr, c_ptr, c_size, c_ptr]),
     "bst_noalloc_scratch_bytes": (c_size, []),
     "bst_plan_set_timing": (c_int, [c_plan, c_int]),
     "bst_plan_timing": (c_int, [c_plan, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), c_int]),

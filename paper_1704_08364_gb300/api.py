@@ -141,6 +141,31 @@ class Plan:
         _check(self._lib.bst_fbp_noalloc(self._h, _ptr(sino), S, _ptr(g), _ptr(out), _stream()), "bst_fbp_noalloc")
         return out
 
+    def fbp_host(self, sino, g=None, out=None, device=None):
+        """BST FBP of a host-resident volume (CPU float32 tensors, ideally pinned)
+        through bst_fbp_host: uploads, kernels and downloads overlap in chunks.
+        Returns `out` once the work is complete."""
+        if not isinstance(sino, torch.Tensor) or sino.is_cuda or sino.dtype != torch.float32 \
+                or not sino.is_contiguous():
+            raise ValueError("sino must be a contiguous float32 CPU tensor")
+        S = sino.shape[0]
+        if tuple(sino.shape) != (S, self.V, self.rays):
+            raise ValueError("sino has the wrong shape")
+        if out is None:
+            out = torch.empty((S, self.rays, self.rays), dtype=torch.float32, pin_memory=sino.is_pinned())
+        if out.is_cuda or out.dtype != torch.float32 or not out.is_contiguous() or \
+                tuple(out.shape) != (S, self.rays, self.rays):
+            raise ValueError("out must be a contiguous float32 CPU tensor of shape [S][N][N]")
+        if g is not None:
+            _need(g, "g", (self.M // 2,))
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        nb = int(self._lib.bst_host_workspace_bytes(self._h, S))
+        ws = self.workspace("host", nb, dev)
+        _check(self._lib.bst_fbp_host(self._h, _ptr(sino), S, _ptr(g), _ptr(out), _ptr(ws), ws.numel(), _stream()),
+               "bst_fbp_host")
+        torch.cuda.current_stream().synchronize()
+        return out
+
     def backproject(self, sino, out=None):
         """Plain BST backprojection (1/sigma weight, zero DC)."""
         return self._forward(sino, None, out, BACKPROJECT)

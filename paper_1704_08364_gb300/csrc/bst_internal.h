@@ -35,6 +35,9 @@ struct bst_plan_s {
     cudaStream_t lane[2] = {nullptr, nullptr};
     cudaEvent_t ev_fork = nullptr;
     cudaEvent_t ev_join[2] = {nullptr, nullptr};
+    // bst_fbp_host: upload and download streams and their events, created on first use
+    cudaStream_t hs[2] = {nullptr, nullptr};
+    cudaEvent_t hev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     // gridding cell lists for the adjoint, built on first use
     int* cell_start = nullptr;      // [(V+1) M + 1]
     int* cell_pts = nullptr;        // [n] index c * M + r of each Cartesian point

@@ -29,6 +29,10 @@ void free_plan(bst_plan_s* p) {
         if (p->ev_join[i]) cudaEventDestroy(p->ev_join[i]);
     }
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    for (int i = 0; i < 2; ++i)
+        if (p->hs[i]) cudaStreamDestroy(p->hs[i]);
+    for (int i = 0; i < 7; ++i)
+        if (p->hev[i]) cudaEventDestroy(p->hev[i]);
     cudaFree(p->tw);
     cudaFree(p->dir);
     cudaFree(p->invdth);

@@ -111,3 +111,19 @@ def test_volume_2048_sampled_slices(bst):
     del d, out
     for n, s in enumerate(idx):
         assert_parity(got[n], ob.fbp(sub[n].astype(np.float64), theta), what=f"volume-2048 slice {s}")
+
+
+def test_host_pipeline_matches_device_path(bst):
+    """bst_fbp_host (chunked upload / reconstruct / download overlap) gives the
+    device path's result; 41 slices of 2048 x 2048 span two staging chunks and
+    end on an odd slice."""
+    S = 41
+    theta, sub, _ = synth.workload_slices("volume-2048", [7, 8])
+    plan = bst.Plan(2048, theta, 2)
+    h = torch.empty((S, 2048, 2048), dtype=torch.float32, pin_memory=True)
+    h[:] = torch.from_numpy(np.resize(sub, (S, 2048, 2048)))
+    h[S - 1] *= -0.5
+    out = plan.fbp_host(h)
+    ref = plan.fbp(h.cuda()).cpu()
+    for s in (0, 1, 31, 32, 33, S - 1):
+        assert_parity(out[s].numpy(), ref[s].numpy(), what=f"host path slice {s}")
