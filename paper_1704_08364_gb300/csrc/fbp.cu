@@ -130,6 +130,8 @@ template <int M, int TPL, int PPT>
 __device__ __forceinline__ void gather_side(const float2* __restrict__ Zp, int V, int q, bool live, int t,
                                             const short* __restrict__ gJq, const float* __restrict__ gFq,
                                             bool mirror, const SmemLine& sm) {
+    constexpr int H = M >> 1;
+    const float2 zero = make_float2(0.f, 0.f);
 #pragma unroll 1
     for (int i = 0; i < PPT; i += 2) {
         float2 z[2][4];
@@ -140,27 +142,61 @@ __device__ __forceinline__ void gather_side(const float2* __restrict__ Zp, int V
             const int ry = signed_freq(ridx, M);
             const int Jt = __ldg(gJq + ridx);
             wt[u] = __ldg(gFq + ridx);
-            Polar P{0, 0.f, 0, 0.f, true};
-            const bool ok = live && Jt >= -1 && polar_radius(q, ry, M, P);
-            const int J = ok ? Jt : 0;
+            // a table bracket >= -1 means the point is inside the band and not the origin
+            const bool ok = live && Jt >= -1;
+            const int rho2 = q * q + ry * ry;
+            const float rf = __fsqrt_rn((float)rho2);
+            int k0 = (int)rf;
+            if (k0 * k0 > rho2) --k0;
+            else if ((k0 + 1) * (k0 + 1) <= rho2) ++k0;
+            const float frac = __fdividef((float)(rho2 - k0 * k0), rf + (float)k0);
+            // kappa = +rho for q >= 0 when r' >= 0; the mirror point has -kappa
+            const bool plus = (ry >= 0) != mirror;
             int K0;
-            radial_bin(P, mirror ? !P.up : P.up, K0, wk[u]);
-            // rows of the bracket; virtual rows -1 and V read rows V-1 and 0 at -k
-            const int rowA = J < 0 ? V - 1 : J;
-            const int sA = J < 0 ? -1 : 1;
-            const int rowB = J + 1 >= V ? 0 : J + 1;
-            const int sB = J + 1 >= V ? -1 : 1;
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int bA = sA * (K0 + c), bB = sB * (K0 + c);
-                const bool vA = ok && bA < (M >> 1) && bA > -(M >> 1);
-                const bool vB = ok && bB < (M >> 1) && bB > -(M >> 1);
-                const size_t oA = vA ? (size_t)rowA * M + (bA < 0 ? bA + M : bA) : 0;
-                const size_t oB = vB ? (size_t)rowB * M + (bB < 0 ? bB + M : bB) : 0;
-                const float2 za = __ldg(Zp + oA), zb = __ldg(Zp + oB);
-                z[u][c] = vA ? za : make_float2(0.f, 0.f);
-                z[u][2 + c] = vB ? zb : make_float2(0.f, 0.f);
+            if (plus) {
+                K0 = k0;
+                wk[u] = frac;
+            } else if (frac > 0.f) {
+                K0 = -k0 - 1;
+                wk[u] = 1.f - frac;
+            } else {
+                K0 = -k0;
+                wk[u] = 0.f;
             }
+            int o00, o01, o10, o11;
+            bool v00, v01, v10, v11;
+            if (ok && Jt >= 0 && Jt <= V - 2 && K0 > -H && K0 < H - 1) {
+                // common case: no seam row, both radial taps inside the band
+                const int k0m = K0 < 0 ? K0 + M : K0;
+                const int k1m = k0m + 1 == M ? 0 : k0m + 1;
+                o00 = Jt * M + k0m;
+                o01 = Jt * M + k1m;
+                o10 = o00 + M;
+                o11 = o01 + M;
+                v00 = v01 = v10 = v11 = true;
+            } else {
+                // rows of the bracket; virtual rows -1 and V read rows V-1 and 0 at -k
+                const int J = ok ? Jt : 0;
+                const int rowA = J < 0 ? V - 1 : J;
+                const int sA = J < 0 ? -1 : 1;
+                const int rowB = J + 1 >= V ? 0 : J + 1;
+                const int sB = J + 1 >= V ? -1 : 1;
+                const int b00 = sA * K0, b01 = sA * (K0 + 1), b10 = sB * K0, b11 = sB * (K0 + 1);
+                v00 = ok && b00 < H && b00 > -H;
+                v01 = ok && b01 < H && b01 > -H;
+                v10 = ok && b10 < H && b10 > -H;
+                v11 = ok && b11 < H && b11 > -H;
+                o00 = v00 ? rowA * M + (b00 < 0 ? b00 + M : b00) : 0;
+                o01 = v01 ? rowA * M + (b01 < 0 ? b01 + M : b01) : 0;
+                o10 = v10 ? rowB * M + (b10 < 0 ? b10 + M : b10) : 0;
+                o11 = v11 ? rowB * M + (b11 < 0 ? b11 + M : b11) : 0;
+            }
+            const float2 a00 = __ldg(Zp + o00), a01 = __ldg(Zp + o01);
+            const float2 a10 = __ldg(Zp + o10), a11 = __ldg(Zp + o11);
+            z[u][0] = v00 ? a00 : zero;
+            z[u][1] = v01 ? a01 : zero;
+            z[u][2] = v10 ? a10 : zero;
+            z[u][3] = v11 ? a11 : zero;
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
