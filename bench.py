@@ -151,6 +151,81 @@ def oracle_slice_time(N: int, V: int, slices: int = 1):
     return time.perf_counter() - t0
 
 
+def _event_ms(fn, steps, warmup=2):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def bench_ragged(bst, synth, sdev, dev, steps):
+    """64 sinograms, rays drawn from {256 ... 2048}, angles = rays, pad 2."""
+    import torch
+    sizes = synth.ragged_sizes()
+    groups = {}
+    for i, N in enumerate(sizes):
+        groups.setdefault(N, []).append(i)
+    plans, sino_g, vol_g = {}, {}, {}
+    for N, idx in groups.items():
+        plans[N] = bst.Plan(N, synth.uniform_angles(N), 2)
+        plans[N].autotune()
+        sino_g[N] = sdev.ellipse_volume(synth.WORKLOADS["ragged-64"].index * 10 + N, len(idx), N, N,
+                                        noise_frac=0.01, device=dev)
+        vol_g[N] = torch.empty((len(idx), N, N), dtype=torch.float32, device=dev)
+    pos = {}
+    for N, idx in groups.items():
+        for k, i in enumerate(idx):
+            pos[i] = (N, k)
+    sinos = [sino_g[pos[i][0]][pos[i][1]] for i in range(len(sizes))]
+    vols = [vol_g[pos[i][0]][pos[i][1]] for i in range(len(sizes))]
+    rb = bst.RaggedBatch([plans[N] for N in sizes]).bind(sinos, vols)
+    voxels = float(sum(N * N for N in sizes))
+
+    def per_size():
+        for N in groups:
+            plans[N].fbp(sino_g[N], out=vol_g[N])
+
+    ms_per_size = _event_ms(per_size, steps)
+    ms_direct = _event_ms(lambda: rb.run(False), steps)
+    ms_graph = _event_ms(lambda: rb.run(True), steps)
+    ok = rb.status() == 0
+    return {"items": len(sizes), "pair_items": rb.pair_items, "voxels": voxels,
+            "schedules": {str(N): plans[N].schedule for N in sorted(plans)},
+            "per_size_ms": ms_per_size, "persistent_ms": ms_direct, "persistent_graph_ms": ms_graph,
+            "persistent_graph_voxels_per_s": voxels / (ms_graph / 1e3), "status_ok": ok}
+
+
+def bench_autograd(bst, synth, dev, steps):
+    """Loss ||FBP(p; g) - f||^2 over 16 slices x 1024 angles x 1024 rays with a
+    learnable 1024-tap filter (init ramp): forward + backward per step."""
+    import torch
+    N = V = 1024
+    theta, p, imgs = synth.workload_slices("autograd-1024", list(range(16)), with_images=True, supersample=1)
+    plan = bst.Plan(N, theta, 2)
+    sino = torch.from_numpy(p).to(dev)
+    f = torch.from_numpy(imgs.astype(np.float32)).to(dev)
+    g = torch.ones(N, device=dev, requires_grad=True)
+    sino.requires_grad_(True)
+
+    def step():
+        g.grad = None
+        sino.grad = None
+        x = bst.fbp_autograd(sino, g, plan)
+        loss = ((x - f) ** 2).sum()
+        loss.backward()
+
+    ms = _event_ms(step, steps)
+    return {"workload": "autograd-1024 (16 x 1024 x 1024, 1024 taps)", "fwd_bwd_ms": ms,
+            "voxels_per_s": 16 * N * N / (ms / 1e3)}
+
+
 def run_reference(args, rank, world):
     N = V = args.rays
     if rank != 0:
@@ -263,6 +338,15 @@ def run_ours(args, rank, world):
     brute_ms_per_slice = b0.elapsed_time(b1) / bs
     bst_ms_per_slice = ms / S
 
+    # the ragged batch: 64 sinograms of mixed sizes, one persistent launch
+    # (direct and replayed from a CUDA graph) vs plain per-size launches
+    ragged = None
+    if not args.no_extras:
+        ragged = bench_ragged(bst, synth, sdev, dev, args.steps)
+        autograd = bench_autograd(bst, synth, dev, args.steps)
+    else:
+        autograd = None
+
     # end to end through the C-ABI host entry point: the step's input in pinned
     # host memory, uploads / kernels / downloads overlapped in chunks, the
     # volume back in pinned host memory, all inside the timed region
@@ -312,6 +396,7 @@ def run_ours(args, rank, world):
             "vs_brute": {"brute_ms_per_slice": brute_ms_per_slice, "bst_ms_per_slice": bst_ms_per_slice,
                          "speedup": brute_ms_per_slice / bst_ms_per_slice, "brute_slices_timed": bs},
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 3 * ((S + 1) // 2) * args.steps,
+            "ragged": ragged, "autograd": autograd,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -329,6 +414,7 @@ def main():
     ap.add_argument("--brute-slices", type=int, default=64)
     ap.add_argument("--e2e-slices", type=int, default=2048)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the ragged-batch and autograd lines")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

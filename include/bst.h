@@ -179,6 +179,52 @@ bst_status_t bst_fbp_host(bst_plan_t plan, const float* h_sino, int slices,
                           const float* d_g, float* h_volume,
                           void* d_ws, size_t ws_bytes, bst_stream_t stream);
 
+/* FFT radix schedule of the plan's forward path: the largest radix of the
+ * Stockham passes, 16 (fewer passes) or 8 (fewer registers per thread).
+ * Results are identical up to rounding.  Errors: INVALID_ARGUMENT. */
+bst_status_t bst_plan_set_schedule(bst_plan_t plan, int max_radix);
+int bst_plan_get_schedule(bst_plan_t plan);
+
+/* Autotuner: time the plan's forward path on a synthetic batch of about
+ * 256 MiB (`slices` slices; <= 0 picks that size) with each radix schedule,
+ * keep the faster one and return it in *chosen.  Allocates and frees its own
+ * buffers; synchronises the device. */
+bst_status_t bst_plan_autotune(bst_plan_t plan, int slices, int* chosen);
+
+/* ---- ragged batch: sinograms of mixed sizes in one persistent launch ----- */
+typedef struct bst_ragged_s* bst_ragged_t;
+
+/* A batch of `items` sinograms, item i reconstructed with plans[i] (plans are
+ * borrowed and must outlive the batch).  Items sharing a plan are paired two
+ * slices per complex line, in order.  Supported FFT lengths: 256, 512, 768,
+ * 1024, 1536, 2048, 3072, 4096.  Errors: INVALID_ARGUMENT, UNSUPPORTED_SIZE,
+ * CUDA, OUT_OF_MEMORY. */
+bst_status_t bst_ragged_create(bst_ragged_t* batch, int items, const bst_plan_t* plans);
+/* Device workspace of the batch: a private Z and T region per pair of items. */
+size_t bst_ragged_workspace_bytes(bst_ragged_t batch);
+/* Number of pair-items (pairs of items sharing a plan, plus unpaired items). */
+int bst_ragged_pair_items(bst_ragged_t batch);
+/* Bind device buffers: d_sinos[i] [V_i][N_i], d_volumes[i] [N_i][N_i] (host
+ * arrays of device pointers), d_g[i] filter taps or NULL (d_g itself may be
+ * NULL: ramp for all; paired items must share their taps).  Builds and
+ * uploads the work queue; drops a captured graph.  flags: 0; bit 0 is a
+ * diagnostic that leaves the ray stage of the first pair-item unqueued, so
+ * that its dependent units wait until the spin limit and the launch reports
+ * BST_ERR_TIMEOUT (used to test the bounded waits). */
+bst_status_t bst_ragged_bind(bst_ragged_t batch, const float* const* d_sinos, const float* const* d_g,
+                             float* const* d_volumes, void* d_ws, size_t ws_bytes, int flags);
+/* Iterations (each with a ~256 ns sleep) a dependency wait may spin before it
+ * gives up with BST_ERR_TIMEOUT (default 2^22, env BST_SPIN_LIMIT). */
+bst_status_t bst_ragged_set_spin_limit(bst_ragged_t batch, int iterations);
+/* Reconstruct the bound batch: one cooperative persistent launch (one block
+ * per SM claims units of the three stages of every item in dependency order).
+ * use_graph != 0: the counter reset and the launch are captured into a CUDA
+ * graph on first use and replayed.  Asynchronous on `stream`. */
+bst_status_t bst_ragged_fbp(bst_ragged_t batch, int use_graph, bst_stream_t stream);
+/* Synchronise `stream`; return and clear the batch's device error (TIMEOUT). */
+bst_status_t bst_ragged_status(bst_ragged_t batch, bst_stream_t stream);
+bst_status_t bst_ragged_destroy(bst_ragged_t batch);
+
 /* Synchronise `stream` and return the plan's sticky device error (BST_OK if
  * none, BST_ERR_CUDA if the stream reported an error). */
 bst_status_t bst_plan_status(bst_plan_t plan, bst_stream_t stream);

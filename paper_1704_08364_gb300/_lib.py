@@ -34,6 +34,18 @@ SIGNATURES = {
     "bst_host_workspace_bytes": (c_size, [c_plan, c_int]),
     "bst_fbp_host": (c_int, [c_plan, c_ptr, c_int, c_ptr, c_ptr, c_ptr, c_size, c_ptr]),
     "bst_noalloc_scratch_bytes": (c_size, []),
+    "bst_plan_set_schedule": (c_int, [c_plan, c_int]),
+    "bst_plan_get_schedule": (c_int, [c_plan]),
+    "bst_plan_autotune": (c_int, [c_plan, c_int, ctypes.POINTER(c_int)]),
+    "bst_ragged_create": (c_int, [ctypes.POINTER(c_ptr), c_int, ctypes.POINTER(c_plan)]),
+    "bst_ragged_workspace_bytes": (c_size, [c_ptr]),
+    "bst_ragged_pair_items": (c_int, [c_ptr]),
+    "bst_ragged_bind": (c_int, [c_ptr, ctypes.POINTER(c_ptr), ctypes.POINTER(c_ptr), ctypes.POINTER(c_ptr), c_ptr,
+                                c_size, c_int]),
+    "bst_ragged_set_spin_limit": (c_int, [c_ptr, c_int]),
+    "bst_ragged_fbp": (c_int, [c_ptr, c_int, c_ptr]),
+    "bst_ragged_status": (c_int, [c_ptr, c_ptr]),
+    "bst_ragged_destroy": (c_int, [c_ptr]),
     "bst_plan_set_timing": (c_int, [c_plan, c_int]),
     "bst_plan_timing": (c_int, [c_plan, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong), c_int]),
 }

@@ -98,6 +98,42 @@ class Plan:
     def status(self):
         _check(self._lib.bst_plan_status(self._h, _stream()), "bst_plan_status")
 
+    @property
+    def schedule(self) -> int:
+        """Largest FFT radix of the forward path's Stockham passes (16 or 8)."""
+        return int(self._lib.bst_plan_get_schedule(self._h))
+
+    @schedule.setter
+    def schedule(self, max_radix: int):
+        _check(self._lib.bst_plan_set_schedule(self._h, int(max_radix)), "bst_plan_set_schedule")
+
+    def autotune(self, slices: int = 0, cache: str | None = None) -> int:
+        """Pick the faster radix schedule by timing both (bst_plan_autotune).
+        With a cache path (default: $BST_AUTOTUNE_CACHE if set) the choice is
+        stored per (GPU name, N, V, pad factor) and reused without timing."""
+        import json
+        import os
+        cache = cache or os.environ.get("BST_AUTOTUNE_CACHE")
+        key = f"{torch.cuda.get_device_name()}|N={self.rays}|V={self.V}|pad={self.pad_factor}"
+        table = {}
+        if cache and os.path.exists(cache):
+            try:
+                with open(cache) as f:
+                    table = json.load(f)
+            except (OSError, ValueError):
+                table = {}
+        if key in table:
+            self.schedule = int(table[key])
+            return self.schedule
+        chosen = ctypes.c_int(0)
+        _check(self._lib.bst_plan_autotune(self._h, int(slices), ctypes.byref(chosen)), "bst_plan_autotune")
+        if cache:
+            table[key] = int(chosen.value)
+            os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
+            with open(cache, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+        return int(chosen.value)
+
     # -- forward -------------------------------------------------------------
 
     def _forward(self, sino, g, out, mode):
@@ -244,3 +280,62 @@ class BstFbpFn(torch.autograd.Function):
 
 def fbp_autograd(sino, g, plan: Plan):
     return BstFbpFn.apply(sino, g, plan)
+
+
+class RaggedBatch:
+    """Sinograms of mixed sizes reconstructed by one persistent launch
+    (bst_ragged_*).  plans[i] is the plan of item i; items sharing a plan are
+    paired.  bind() fixes the device buffers; run() launches (optionally from a
+    captured CUDA graph)."""
+
+    def __init__(self, plans):
+        self._lib = _lib.load()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(self._lib.bst_ragged_create(ctypes.byref(h), len(self.plans), arr), "bst_ragged_create")
+        self._h = h
+        self._ws = None
+        self._bound = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                self._lib.bst_ragged_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    @property
+    def pair_items(self) -> int:
+        return int(self._lib.bst_ragged_pair_items(self._h))
+
+    def bind(self, sinos, volumes, gs=None, flags: int = 0):
+        n = len(self.plans)
+        if len(sinos) != n or len(volumes) != n:
+            raise ValueError("one sinogram and one volume per item")
+        for p, sg, v in zip(self.plans, sinos, volumes):
+            _need(sg, "sino", (p.V, p.rays))
+            _need(v, "volume", (p.rays, p.rays))
+        nb = int(self._lib.bst_ragged_workspace_bytes(self._h))
+        dev = sinos[0].device
+        if self._ws is None or self._ws.numel() < nb:
+            self._ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+        s_arr = (ctypes.c_void_p * n)(*[t.data_ptr() for t in sinos])
+        v_arr = (ctypes.c_void_p * n)(*[t.data_ptr() for t in volumes])
+        g_arr = None if gs is None else (ctypes.c_void_p * n)(*[0 if g is None else g.data_ptr() for g in gs])
+        _check(self._lib.bst_ragged_bind(self._h, s_arr, g_arr, v_arr, _ptr(self._ws), self._ws.numel(), int(flags)),
+               "bst_ragged_bind")
+        self._bound = (list(sinos), list(volumes), gs)   # keep the buffers alive
+        return self
+
+    def set_spin_limit(self, iterations: int):
+        _check(self._lib.bst_ragged_set_spin_limit(self._h, int(iterations)), "bst_ragged_set_spin_limit")
+
+    def run(self, use_graph: bool = False):
+        _check(self._lib.bst_ragged_fbp(self._h, int(bool(use_graph)), _stream()), "bst_ragged_fbp")
+
+    def status(self) -> int:
+        """Synchronise; return (and clear) the device status code (0 = ok)."""
+        return int(self._lib.bst_ragged_status(self._h, _stream()))

@@ -126,13 +126,16 @@ template <bool INV> struct Dft<16, INV> {
 // ---- radix schedule --------------------------------------------------------
 
 __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
-// Radix of pass p for length M = 3^b 2^a (b <= 1): one radix-3 pass first,
-// then ceil(a/4) power-of-two passes of as equal a size as possible.
-__host__ __device__ constexpr int radix_of(int M, int p) {
+// Radix of pass p for length M = 3^b 2^a (b <= 1) with radices at most MAXR
+// (16 or 8): one radix-3 pass first, then ceil(a / log2 MAXR) power-of-two
+// passes of as equal a size as possible.  The maximum radix is the schedule
+// the autotuner chooses between.
+__host__ __device__ constexpr int radix_of(int M, int p, int MAXR = 16) {
     const bool three = (M % 3 == 0);
     if (three && p == 0) return 3;
     const int a = ilog2c(three ? M / 3 : M);
-    const int passes = (a + 3) / 4;
+    const int rb = ilog2c(MAXR);
+    const int passes = (a + rb - 1) / rb;
     const int q = p - (three ? 1 : 0);
     const int bits = a / passes + (q < a % passes ? 1 : 0);
     return 1 << bits;
@@ -228,10 +231,10 @@ __device__ __forceinline__ void stockham_pass(int t, const Src& src, const Dst& 
 // Run passes PIDX.. of the length-M transform.  Pass 0 reads `src`, the last
 // pass writes `dst`; the others go through the shared-memory line `sm`.
 // Every thread of the block must call this (it contains __syncthreads()).
-template <int M, int TPL, bool INV, int PIDX, int NS, class Src, class Dst>
+template <int M, int TPL, bool INV, int MAXR, int PIDX, int NS, class Src, class Dst>
 __device__ __forceinline__ void fft_run(int t, const Src& src, const Dst& dst, const SmemLine& sm,
                                         const float2* __restrict__ tw) {
-    constexpr int R = radix_of(M, PIDX);
+    constexpr int R = radix_of(M, PIDX, MAXR);
     constexpr bool LAST = (NS * R == M);
     if constexpr (PIDX == 0) {
         if constexpr (LAST) {
@@ -239,7 +242,7 @@ __device__ __forceinline__ void fft_run(int t, const Src& src, const Dst& dst, c
         } else {
             stockham_pass<M, R, NS, TPL, INV>(t, src, sm, tw, Src::kSmem);
             __syncthreads();
-            fft_run<M, TPL, INV, PIDX + 1, NS * R>(t, src, dst, sm, tw);
+            fft_run<M, TPL, INV, MAXR, PIDX + 1, NS * R>(t, src, dst, sm, tw);
         }
     } else {
         if constexpr (LAST) {
@@ -247,15 +250,15 @@ __device__ __forceinline__ void fft_run(int t, const Src& src, const Dst& dst, c
         } else {
             stockham_pass<M, R, NS, TPL, INV>(t, sm, sm, tw, true);
             __syncthreads();
-            fft_run<M, TPL, INV, PIDX + 1, NS * R>(t, src, dst, sm, tw);
+            fft_run<M, TPL, INV, MAXR, PIDX + 1, NS * R>(t, src, dst, sm, tw);
         }
     }
 }
 
-template <int M, int TPL, bool INV, class Src, class Dst>
+template <int M, int TPL, bool INV, int MAXR = 16, class Src, class Dst>
 __device__ __forceinline__ void fft_line(int t, const Src& src, const Dst& dst, const SmemLine& sm,
                                          const float2* __restrict__ tw) {
-    fft_run<M, TPL, INV, 0, 1>(t, src, dst, sm, tw);
+    fft_run<M, TPL, INV, MAXR, 0, 1>(t, src, dst, sm, tw);
 }
 
 // signed frequency of natural-order index p

@@ -30,6 +30,7 @@ struct bst_plan_s {
     short* geo_J = nullptr;
     float* geo_f = nullptr;
     int chunk_pairs = 1;            // slice pairs per chunk of the forward path
+    int maxr = 16;                  // FFT radix schedule of the forward path (16 or 8; autotuned)
     // two plan-owned streams that alternate chunks of the forward path (fork
     // from and join back to the caller's stream with events), created on first use
     cudaStream_t lane[2] = {nullptr, nullptr};

@@ -1,0 +1,291 @@
+// bst_stages.cuh -- the three stages of the BST forward path as device
+// functions over "units" (a few lines of one slice pair), shared by the
+// per-size kernels of fbp.cu and the persistent ragged kernel of ragged.cu.
+//
+//   ray_unit   stages P2 + P3 + P4 for LPC angles j0.. of a pair: centre-aligned
+//              zero padding of the rays to M, forward FFT along t, weight W[|k|],
+//              written to Z[V][M] (natural order).
+//   grid_unit  stages P0 + P5 + the column half of P6 for CPC Cartesian column
+//              pairs (q, -q), q = q0..: bilinear gather from Z with the plan's
+//              angular geometry table, inverse FFT along r', the N central rows
+//              written to T.
+//   row_unit   the row half of P6 + P7 + P8 for TPC blocks of four rows: inverse
+//              FFT along c', the N central columns scaled by dt dw^2 = N/(2 M^2),
+//              Re to slice a and Im to slice b.
+//
+// Every thread of the block calls the unit (the FFT passes contain barriers).
+// MAXR is the radix schedule (largest radix 16 or 8) chosen per FFT length.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "bst_fft.cuh"
+#include "bst_geo.cuh"
+#include "bst_internal.h"
+
+namespace bst {
+
+// threads per line: 16 elements per thread (12 for lengths 3 * 2^a)
+template <int M> __host__ __device__ constexpr int tpl_of() { return (M % 3 == 0) ? M / 12 : M / 16; }
+
+struct RaySrc {
+    const float* ya;
+    const float* yb;
+    int N, M;
+    bool live;
+    static constexpr bool kSmem = false;
+    __device__ __forceinline__ float2 load(int m) const {
+        int i = m + (N >> 1);
+        if (i >= M) i -= M;
+        if (!live || i >= N) return make_float2(0.f, 0.f);
+        return make_float2(__ldg(ya + i), yb ? __ldg(yb + i) : 0.f);
+    }
+};
+
+struct SpecDst {
+    float2* z;
+    const float* g;
+    int M, mode;
+    float two_alpha;
+    bool live;
+    static constexpr bool kSmem = false;
+    __device__ __forceinline__ void store(int k, float2 v) const {
+        if (!live) return;
+        const int ak = k <= (M >> 1) ? k : M - k;
+        float w;
+        if (mode == BSTK_RAW) w = 1.f;
+        else if (ak == (M >> 1)) w = 0.f;
+        else if (mode == BSTK_FILTER) w = g ? __ldg(g + ak) : 1.f;
+        else w = ak == 0 ? 0.f : __fdiv_rn(two_alpha, (float)ak);
+        z[k] = make_float2(v.x * w, v.y * w);
+    }
+};
+
+// T layout per pair: [ceil(N/4)][M][4] complex, row r of the kept band at
+// (r / 4, c', r % 4): a column write fills whole 32-byte sectors and a
+// four-row block is contiguous for k_row_ifft.
+struct ColDst {
+    float2* T;
+    int N, M, cidx;
+    bool rev, live;
+    static constexpr bool kSmem = false;
+    __device__ __forceinline__ void store(int p, float2 v) const {
+        if (!live) return;
+        const int q = rev ? (p == 0 ? 0 : M - p) : p;
+        const int r = signed_freq(q, M) + (N >> 1);
+        if (r < 0 || r >= N) return;
+        T[((size_t)(r >> 2) * M + cidx) * 4 + (r & 3)] = v;
+    }
+};
+
+// Bilinear gather of one side of a column pair: plus = true for the point
+// (q, r') itself (kappa = +rho when P.up), false for its mirror (-q, -r').
+// Two points per step; all eight tap loads are issued before any is used.
+template <int M, int TPL, int PPT>
+__device__ __forceinline__ void gather_side(const float2* __restrict__ Zp, int V, int q, bool live, int t,
+                                            const short* __restrict__ gJq, const float* __restrict__ gFq,
+                                            bool mirror, const SmemLine& sm) {
+    constexpr int H = M >> 1;
+    const float2 zero = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int i = 0; i < PPT; i += 2) {
+        float2 z[2][4];
+        float wk[2], wt[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int ridx = t + (i + u) * TPL;
+            const int ry = signed_freq(ridx, M);
+            const int Jt = __ldg(gJq + ridx);
+            wt[u] = __ldg(gFq + ridx);
+            // a table bracket >= -1 means the point is inside the band and not the origin
+            const bool ok = live && Jt >= -1;
+            const int rho2 = q * q + ry * ry;
+            const float rf = __fsqrt_rn((float)rho2);
+            int k0 = (int)rf;
+            if (k0 * k0 > rho2) --k0;
+            else if ((k0 + 1) * (k0 + 1) <= rho2) ++k0;
+            const float frac = __fdividef((float)(rho2 - k0 * k0), rf + (float)k0);
+            // kappa = +rho for q >= 0 when r' >= 0; the mirror point has -kappa
+            const bool plus = (ry >= 0) != mirror;
+            int K0;
+            if (plus) {
+                K0 = k0;
+                wk[u] = frac;
+            } else if (frac > 0.f) {
+                K0 = -k0 - 1;
+                wk[u] = 1.f - frac;
+            } else {
+                K0 = -k0;
+                wk[u] = 0.f;
+            }
+            int o00, o01, o10, o11;
+            bool v00, v01, v10, v11;
+            if (ok && Jt >= 0 && Jt <= V - 2 && K0 > -H && K0 < H - 1) {
+                // common case: no seam row, both radial taps inside the band
+                const int k0m = K0 < 0 ? K0 + M : K0;
+                const int k1m = k0m + 1 == M ? 0 : k0m + 1;
+                o00 = Jt * M + k0m;
+                o01 = Jt * M + k1m;
+                o10 = o00 + M;
+                o11 = o01 + M;
+                v00 = v01 = v10 = v11 = true;
+            } else {
+                // rows of the bracket; virtual rows -1 and V read rows V-1 and 0 at -k
+                const int J = ok ? Jt : 0;
+                const int rowA = J < 0 ? V - 1 : J;
+                const int sA = J < 0 ? -1 : 1;
+                const int rowB = J + 1 >= V ? 0 : J + 1;
+                const int sB = J + 1 >= V ? -1 : 1;
+                const int b00 = sA * K0, b01 = sA * (K0 + 1), b10 = sB * K0, b11 = sB * (K0 + 1);
+                v00 = ok && b00 < H && b00 > -H;
+                v01 = ok && b01 < H && b01 > -H;
+                v10 = ok && b10 < H && b10 > -H;
+                v11 = ok && b11 < H && b11 > -H;
+                o00 = v00 ? rowA * M + (b00 < 0 ? b00 + M : b00) : 0;
+                o01 = v01 ? rowA * M + (b01 < 0 ? b01 + M : b01) : 0;
+                o10 = v10 ? rowB * M + (b10 < 0 ? b10 + M : b10) : 0;
+                o11 = v11 ? rowB * M + (b11 < 0 ? b11 + M : b11) : 0;
+            }
+            const float2 a00 = __ldg(Zp + o00), a01 = __ldg(Zp + o01);
+            const float2 a10 = __ldg(Zp + o10), a11 = __ldg(Zp + o11);
+            z[u][0] = v00 ? a00 : zero;
+            z[u][1] = v01 ? a01 : zero;
+            z[u][2] = v10 ? a10 : zero;
+            z[u][3] = v11 ? a11 : zero;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const float fk = wk[u], ft = wt[u];
+            const float2 z00 = z[u][0], z01 = z[u][1], z10 = z[u][2], z11 = z[u][3];
+            const float2 a = make_float2(fmaf(fk, z01.x - z00.x, z00.x), fmaf(fk, z01.y - z00.y, z00.y));
+            const float2 b = make_float2(fmaf(fk, z11.x - z10.x, z10.x), fmaf(fk, z11.y - z10.y, z10.y));
+            sm.store(t + (i + u) * TPL, make_float2(fmaf(ft, b.x - a.x, a.x), fmaf(ft, b.y - a.y, a.y)));
+        }
+    }
+}
+
+struct TileSrc {
+    const float2* T;
+    int M, rb, line;
+    bool live;
+    static constexpr bool kSmem = false;
+    __device__ __forceinline__ float2 load(int c) const {
+        return live ? __ldg(T + ((size_t)rb * M + c) * 4 + line) : make_float2(0.f, 0.f);
+    }
+};
+
+struct VolDst {
+    float* va;
+    float* vb;
+    int N, M;
+    float scale;
+    bool live;
+    static constexpr bool kSmem = false;
+    __device__ __forceinline__ void store(int p, float2 v) const {
+        if (!live) return;
+        const int c = signed_freq(p, M) + (N >> 1);
+        if (c < 0 || c >= N) return;
+        va[c] = v.x * scale;
+        if (vb) vb[c] = v.y * scale;
+    }
+};
+
+template <int M> __host__ __device__ constexpr int row_line_stride() { return smem_line_len(M) + 4; }
+
+
+
+// P2 + P3 + P4 for lines j0 .. j0 + LPC - 1 of one slice pair (blockDim = TPL * LPC)
+template <int M, int TPL, int LPC, int MAXR>
+__device__ __forceinline__ void ray_unit(float2* smem, int j0, int V, int N, const float* __restrict__ ya,
+                                         const float* __restrict__ yb, int mode, const float* __restrict__ g,
+                                         float two_alpha, float2* __restrict__ Zp, const float2* __restrict__ tw) {
+    const int line = threadIdx.x / TPL, t = threadIdx.x % TPL;
+    const int j = j0 + line;
+    const bool live = j < V;
+    const int jj = live ? j : 0;
+    RaySrc src{ya + (size_t)jj * N, yb ? yb + (size_t)jj * N : nullptr, N, M, live};
+    SpecDst dst{Zp + (size_t)jj * M, g, M, mode, two_alpha, live};
+    SmemLine sm{smem + line * smem_line_len(M)};
+    fft_line<M, TPL, false, MAXR>(t, src, dst, sm, tw);
+}
+
+// P0 + P5 + column P6 for column pairs q0 .. q0 + CPC - 1 (blockDim = TPL * CPC):
+// first column q, then its mirror -q (the same angular geometry; stored
+// index-reversed, its transform is read back reversed; column -M/2 pairs with
+// q = 0 and is zero).  Consecutive lanes take consecutive rows, so a warp's taps
+// fall on neighbouring polar samples.
+template <int M, int TPL, int CPC, int MAXR>
+__device__ __forceinline__ void grid_unit(float2* smem, int q0, int V, int N, const float2* __restrict__ Zp,
+                                          const short* __restrict__ gJ, const float* __restrict__ gF,
+                                          float2* __restrict__ Tp, const float2* __restrict__ tw) {
+    constexpr int PPT = M / TPL;   // Cartesian points per thread and column
+    static_assert(PPT % 2 == 0, "points per thread");
+    const int cp = threadIdx.x / TPL;
+    const int t = threadIdx.x % TPL;
+    const int q = q0 + cp;
+    const bool live = q < (M >> 1);
+    const SmemLine sm{smem + cp * smem_line_len(M)};
+    const short* gJq = gJ + (size_t)(live ? q : 0) * M;
+    const float* gFq = gF + (size_t)(live ? q : 0) * M;
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        if (side == 0 || q != 0) {
+            gather_side<M, TPL, PPT>(Zp, V, q, live, t, gJq, gFq, side == 1, sm);
+        } else {
+            for (int i = 0; i < PPT; ++i) sm.store(t + i * TPL, make_float2(0.f, 0.f));
+        }
+        // the origin is single-valued: mean over angles of the DC bin
+        if (side == 0 && live && q == 0) {
+            if constexpr (TPL >= 32) {
+                if (t < 32) {
+                    float sx = 0.f, sy = 0.f;
+                    for (int j = t; j < V; j += 32) {
+                        const float2 zz = __ldg(Zp + (size_t)j * M);
+                        sx += zz.x;
+                        sy += zz.y;
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                    }
+                    if (t == 0) sm.store(0, make_float2(sx / (float)V, sy / (float)V));
+                }
+            } else {
+                if (t == 0) {
+                    float sx = 0.f, sy = 0.f;
+                    for (int j = 0; j < V; ++j) {
+                        const float2 zz = __ldg(Zp + (size_t)j * M);
+                        sx += zz.x;
+                        sy += zz.y;
+                    }
+                    sm.store(0, make_float2(sx / (float)V, sy / (float)V));
+                }
+            }
+        }
+        __syncthreads();
+        const ColDst dst{Tp, N, M, side == 0 ? q : (q == 0 ? (M >> 1) : M - q), side == 1 && q != 0, live};
+        fft_line<M, TPL, true, MAXR>(t, sm, dst, sm, tw);
+        __syncthreads();
+    }
+}
+
+// row P6 + P7 + P8 for row blocks rb0 .. rb0 + TPC - 1 of four rows (blockDim = 4 TPL TPC);
+// va, vb: the [N][N] images of slices a and b (vb may be null)
+template <int M, int TPL, int TPC, int MAXR>
+__device__ __forceinline__ void row_unit(float2* smem, int rb0, int N, const float2* __restrict__ Tp,
+                                         float* __restrict__ va, float* __restrict__ vb, float scale,
+                                         const float2* __restrict__ tw) {
+    const int tile = threadIdx.x / (4 * TPL);
+    const int w = threadIdx.x % (4 * TPL);
+    const int line = w & 3, t = w >> 2;
+    const int rb = rb0 + tile;
+    const int r = rb * 4 + line;
+    const bool live = r < N;
+    const int rr = live ? r : 0;
+    TileSrc src{Tp, M, live ? rb : 0, line, live};
+    VolDst dst{va + (size_t)rr * N, vb ? vb + (size_t)rr * N : nullptr, N, M, scale, live};
+    SmemLine sm{smem + (tile * 4 + line) * row_line_stride<M>()};
+    fft_line<M, TPL, true, MAXR>(t, src, dst, sm, tw);
+}
+
+}  // namespace bst

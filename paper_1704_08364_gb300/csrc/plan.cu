@@ -310,6 +310,67 @@ bst_status_t brute_backproject(bst_plan_t p, const float* d_sino, int slices, co
     return bst_launch_brute(p, d_sino, slices, d_g, d_volume, d_ws, ws_bytes, (cudaStream_t)stream);
 }
 
+bst_status_t bst_plan_set_schedule(bst_plan_t p, int max_radix) {
+    if (!p || (max_radix != 8 && max_radix != 16)) return BST_ERR_INVALID_ARGUMENT;
+    p->maxr = max_radix;
+    return BST_OK;
+}
+
+int bst_plan_get_schedule(bst_plan_t p) { return p ? p->maxr : 0; }
+
+bst_status_t bst_plan_autotune(bst_plan_t p, int slices, int* chosen) {
+    if (!p) return BST_ERR_INVALID_ARGUMENT;
+    if (slices <= 0) {
+        const size_t per = (size_t)p->V * p->N * sizeof(float);
+        slices = (int)std::max<size_t>(2, std::min<size_t>(4096, (((size_t)256 << 20) / per) & ~(size_t)1));
+    }
+    const size_t nin = (size_t)slices * p->V * p->N, nout = (size_t)slices * p->N * p->N;
+    const size_t nws = bst_workspace_bytes(p, slices);
+    float *in = nullptr, *out = nullptr;
+    void* ws = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    bst_status_t st = BST_OK;
+    if (cudaMalloc((void**)&in, nin * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void**)&out, nout * sizeof(float)) != cudaSuccess || cudaMalloc(&ws, nws) != cudaSuccess) {
+        st = BST_ERR_OUT_OF_MEMORY;
+    }
+    if (st == BST_OK && (cudaMemset(in, 0, nin * sizeof(float)) != cudaSuccess ||
+                         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        st = BST_ERR_CUDA;
+    const int old = p->maxr;
+    const bool timing = p->timing;
+    p->timing = false;
+    int best = old;
+    float best_ms = 1e30f;
+    const int cand[2] = {16, 8};
+    for (int c = 0; st == BST_OK && c < 2; ++c) {
+        p->maxr = cand[c];
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 4 && st == BST_OK; ++rep) {
+            cudaEventRecord(e0, nullptr);
+            st = bst_launch_forward(p, in, slices, BSTK_FILTER, nullptr, out, ws, nws, nullptr);
+            cudaEventRecord(e1, nullptr);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = BST_ERR_CUDA;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_min = std::min(ms_min, ms);   // the first run warms up
+        }
+        if (st == BST_OK && ms_min < best_ms) {
+            best_ms = ms_min;
+            best = cand[c];
+        }
+    }
+    p->maxr = st == BST_OK ? best : old;
+    p->timing = timing;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(in);
+    cudaFree(out);
+    cudaFree(ws);
+    if (chosen) *chosen = p->maxr;
+    return st;
+}
+
 bst_status_t bst_plan_status(bst_plan_t p, bst_stream_t stream) {
     if (!p) return BST_ERR_INVALID_ARGUMENT;
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return BST_ERR_CUDA;
