@@ -95,6 +95,26 @@ bst_status_t bst_backproject(bst_plan_t plan, const float* d_sino, int slices,
                              float* d_volume, void* d_ws, size_t ws_bytes,
                              bst_stream_t stream);
 
+/* BST filtered backprojection with the pre-reconstruction stages fused into
+ * its first stage (the paper's stages N and C of Sec. 3, and window P1):
+ *   normalization (Sec. 1 (a)), when d_flat != NULL: d_sino holds photon
+ *     counts I and y = -log[(I - D)/(I0 - D)], both differences clamped to
+ *     >= 1e-6; d_flat (I0) and d_dark (D, or NULL for 0) are [slices][N],
+ *     the detector row of each slice;
+ *   centering (Sec. 1 (b)): the measured rays are y(t - beta); they are
+ *     shifted back by `shift` = beta in detector samples (|shift| < N) with
+ *     the exact band-limited shift on the padded grid (spectrum times
+ *     exp(+2 pi i k shift / M));
+ *   window (P1): kb_beta > 0 multiplies the centered rays by the
+ *     Kaiser-Bessel window I0(kb_beta sqrt(1 - (t/h)^2)) / I0(kb_beta),
+ *     |t| <= h = kb_halfwidth (detector units, t in [-1, 1)).
+ * All zero/NULL: identical to bst_fbp.  Other arguments as bst_fbp.
+ * Errors: INVALID_ARGUMENT, WORKSPACE_TOO_SMALL, CUDA. */
+bst_status_t bst_fbp_prep(bst_plan_t plan, const float* d_sino, int slices,
+                          const float* d_dark, const float* d_flat, float shift,
+                          float kb_beta, float kb_halfwidth, const float* d_g,
+                          float* d_volume, void* d_ws, size_t ws_bytes, bst_stream_t stream);
+
 /* Device workspace in bytes for radon_adjoint and bst_fbp_filter_grad. */
 size_t bst_adjoint_workspace_bytes(bst_plan_t plan, int slices);
 

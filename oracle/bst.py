@@ -197,6 +197,13 @@ def bst(y: np.ndarray, angles, pad_factor: int = 2, mode: str = FILTER, g=None,
     M = pad_factor * N
     angles64(angles)
     Y = ray_spectrum(y, M, direct)                                 # P2, P3
+    return bst_from_spectrum(Y, angles, N, mode, g, direct, return_pad)
+
+
+def bst_from_spectrum(Y: np.ndarray, angles, N: int, mode: str = FILTER, g=None,
+                      direct: bool = False, return_pad: bool = False):
+    """Stages P4-P8 applied to the ray spectrum Y[V][M] of P3."""
+    M = Y.shape[-1]
     Z = mean_dc(apply_weight(Y, weight_table(M, N, mode, g)))      # P4
     X = grid(Z, angles)                                            # P0, P5
     vol, xp = image_from_grid(X, N, direct)                        # P6-P8

@@ -22,6 +22,8 @@ SIGNATURES = {
     "bst_workspace_bytes": (c_size, [c_plan, c_int]),
     "bst_fbp": (c_int, [c_plan, c_ptr, c_int, c_ptr, c_ptr, c_ptr, c_size, c_ptr]),
     "bst_backproject": (c_int, [c_plan, c_ptr, c_int, c_ptr, c_ptr, c_size, c_ptr]),
+    "bst_fbp_prep": (c_int, [c_plan, c_ptr, c_int, c_ptr, c_ptr, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                             c_ptr, c_ptr, c_ptr, c_size, c_ptr]),
     "bst_adjoint_workspace_bytes": (c_size, [c_plan, c_int]),
     "radon_adjoint": (c_int, [c_plan, c_int, c_ptr, c_ptr, c_int, c_ptr, c_ptr, c_size, c_ptr]),
     "bst_fbp_filter_grad": (c_int, [c_plan, c_ptr, c_ptr, c_int, c_ptr, c_ptr, c_size, c_ptr]),

@@ -161,6 +161,28 @@ class Plan:
         """BST filtered backprojection of sino [S][V][N] -> [S][N][N]."""
         return self._forward(sino, g, out, FILTER)
 
+    def fbp_prep(self, sino, flat=None, dark=None, shift: float = 0.0, kb_beta: float = 0.0,
+                 kb_halfwidth: float = 1.0, g=None, out=None):
+        """bst_fbp_prep: normalization from counts (flat/dark rows [S][N]),
+        centering by `shift` detector samples and the Kaiser-Bessel window P1,
+        fused into the ray stage of the filtered backprojection."""
+        _need(sino, "sino")
+        S = sino.shape[0]
+        _need(sino, "sino", (S, self.V, self.rays))
+        for t, name in ((flat, "flat"), (dark, "dark")):
+            if t is not None:
+                _need(t, name, (S, self.rays))
+        if g is not None:
+            _need(g, "g", (self.M // 2,))
+        if out is None:
+            out = torch.empty((S, self.rays, self.rays), dtype=torch.float32, device=sino.device)
+        _need(out, "out", (S, self.rays, self.rays))
+        ws = self.workspace("fwd", self.workspace_bytes(S), sino.device)
+        _check(self._lib.bst_fbp_prep(self._h, _ptr(sino), S, _ptr(dark), _ptr(flat), float(shift), float(kb_beta),
+                                      float(kb_halfwidth), _ptr(g), _ptr(out), _ptr(ws), ws.numel(), _stream()),
+               "bst_fbp_prep")
+        return out
+
     def fbp_noalloc(self, sino, g=None, out=None):
         """As fbp, through bst_fbp_noalloc: the library's fixed scratch array
         instead of a workspace (the output tensor is still the caller's)."""

@@ -99,6 +99,12 @@ bst_status_t bst_launch_forward(bst_plan_s* p, const float* sino, int slices, in
 // workspace and up to `lanes` (1 or 2) streams alternating the chunks
 bst_status_t bst_launch_forward_chunked(bst_plan_s* p, const float* sino, int slices, int mode, const float* g,
                                         float* vol, void* ws, cudaStream_t st, int max_chunk, int lanes);
+namespace bst {
+struct PrepArgs;
+}
+// as bst_launch_forward (filter mode) with the pre-reconstruction stages in the ray kernel
+bst_status_t bst_launch_forward_prep(bst_plan_s* p, const float* sino, int slices, const bst::PrepArgs& prep,
+                                     const float* g, float* vol, void* ws, size_t ws_bytes, cudaStream_t st);
 // create the plan's two chunk streams and their events (false on failure)
 bool bst_ensure_lanes(bst_plan_s* p);
 bst_status_t bst_launch_adjoint(bst_plan_s* p, int mode, const float* g, const float* vol, int slices,

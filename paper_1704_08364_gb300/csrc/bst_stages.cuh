@@ -191,7 +191,105 @@ struct VolDst {
 
 template <int M> __host__ __device__ constexpr int row_line_stride() { return smem_line_len(M) + 4; }
 
+// ---- pre-reconstruction stages fused into the ray load and the weight ------
+//
+// Normalization (Sec. 1 (a)): y = -log[(I - D)/(I0 - D)] from counts I with the
+// slice's flat row I0 and dark row D (both differences clamped to >= 1e-6).
+// Window (stage P1): y_i *= w(t_i - shift dt), a Kaiser-Bessel window
+// I0(b sqrt(1 - (t/h)^2)) / I0(b) for |t| <= h.  Centering (Sec. 1 (b)): the
+// spectrum is multiplied by exp(+2 pi i k shift / M), the exact shift of the
+// padded ray by `shift` samples.
+struct PrepArgs {
+    const float* dark;    // [S][N] or null (0)
+    const float* flat;    // [S][N] or null (input is already y)
+    float shift;          // centering shift in detector samples
+    int shift_int;        // its integer part ...
+    float shift_frac;     // ... and fraction (exact phase reduction)
+    float kb_beta;        // window shape (0: no window)
+    float kb_inv_half;    // 1 / half-width (detector units)
+    float kb_norm;        // 1 / I0(kb_beta)
+};
 
+struct RaySrcPrep {
+    const float* ya;
+    const float* yb;
+    const float* da;
+    const float* db;
+    const float* fa;
+    const float* fb;
+    int N, M;
+    bool live;
+    PrepArgs pa;
+    static constexpr bool kSmem = false;
+    __device__ __forceinline__ float sample(const float* y, const float* d, const float* f, int i) const {
+        float v = __ldg(y + i);
+        if (f) {
+            const float dk = d ? __ldg(d + i) : 0.f;
+            v = -logf(fmaxf(v - dk, 1e-6f) / fmaxf(__ldg(f + i) - dk, 1e-6f));
+        }
+        return v;
+    }
+    __device__ __forceinline__ float2 load(int m) const {
+        int i = m + (N >> 1);
+        if (i >= M) i -= M;
+        if (!live || i >= N) return make_float2(0.f, 0.f);
+        float w = 1.f;
+        if (pa.kb_beta > 0.f) {
+            const float t = ((float)(i - (N >> 1)) - pa.shift) * (2.f / (float)N);
+            const float u = t * pa.kb_inv_half;
+            w = fabsf(u) <= 1.f ? cyl_bessel_i0f(pa.kb_beta * sqrtf(fmaxf(1.f - u * u, 0.f))) * pa.kb_norm : 0.f;
+        }
+        return make_float2(w * sample(ya, da, fa, i), yb ? w * sample(yb, db, fb, i) : 0.f);
+    }
+};
+
+struct SpecDstShift {
+    float2* z;
+    const float* g;
+    int M, mode;
+    float two_alpha;
+    bool live;
+    PrepArgs pa;
+    static constexpr bool kSmem = false;
+    __device__ __forceinline__ void store(int k, float2 v) const {
+        if (!live) return;
+        const int ak = k <= (M >> 1) ? k : M - k;
+        float w;
+        if (ak == (M >> 1)) w = 0.f;
+        else if (mode == BSTK_FILTER) w = g ? __ldg(g + ak) : 1.f;
+        else w = ak == 0 ? 0.f : __fdiv_rn(two_alpha, (float)ak);
+        if (pa.shift != 0.f) {
+            // exp(+2 pi i k s / M) with s = s_int + s_frac; the integer part reduced exactly mod M
+            const int ks = signed_freq(k, M);
+            int m = (int)(((long long)ks * pa.shift_int) % M);
+            if (m < 0) m += M;
+            float s1, c1, s2, c2;
+            sincospif(2.f * (float)m / (float)M, &s1, &c1);
+            sincospif(2.f * (float)ks * pa.shift_frac / (float)M, &s2, &c2);
+            const float c = c1 * c2 - s1 * s2, sn = s1 * c2 + c1 * s2;
+            v = make_float2(v.x * c - v.y * sn, v.x * sn + v.y * c);
+        }
+        z[k] = make_float2(v.x * w, v.y * w);
+    }
+};
+
+// ray_unit with the pre-reconstruction stages (slice rows da/db, fa/fb of the
+// dark and flat fields, or null)
+template <int M, int TPL, int LPC, int MAXR>
+__device__ __forceinline__ void ray_unit_prep(float2* smem, int j0, int V, int N, const float* __restrict__ ya,
+                                              const float* __restrict__ yb, const float* da, const float* db,
+                                              const float* fa, const float* fb, const PrepArgs& pa, int mode,
+                                              const float* __restrict__ g, float two_alpha,
+                                              float2* __restrict__ Zp, const float2* __restrict__ tw) {
+    const int line = threadIdx.x / TPL, t = threadIdx.x % TPL;
+    const int j = j0 + line;
+    const bool live = j < V;
+    const int jj = live ? j : 0;
+    RaySrcPrep src{ya + (size_t)jj * N, yb ? yb + (size_t)jj * N : nullptr, da, db, fa, fb, N, M, live, pa};
+    SpecDstShift dst{Zp + (size_t)jj * M, g, M, mode, two_alpha, live, pa};
+    SmemLine sm{smem + line * smem_line_len(M)};
+    fft_line<M, TPL, false, MAXR>(t, src, dst, sm, tw);
+}
 
 // P2 + P3 + P4 for lines j0 .. j0 + LPC - 1 of one slice pair (blockDim = TPL * LPC)
 template <int M, int TPL, int LPC, int MAXR>

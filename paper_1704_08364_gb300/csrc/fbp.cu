@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstdint>
 
 #include "bst_stages.cuh"
 
@@ -57,6 +59,22 @@ __global__ void k_geo_table(Geo geo, int M, short* __restrict__ gJ, float* __res
     }
     gJ[idx] = J;
     gF[idx] = f;
+}
+
+template <int M, int TPL, int LPC, int MAXR>
+__global__ void __launch_bounds__(TPL * LPC)
+    k_ray_fft_prep(const float* __restrict__ sino, int slices, int pair0, int N, int V, PrepArgs pa, int mode,
+                   const float* __restrict__ g, float two_alpha, float2* __restrict__ Z,
+                   const float2* __restrict__ tw) {
+    extern __shared__ float2 smem[];
+    const int pl = blockIdx.y;
+    const int sa = 2 * (pair0 + pl), sb = sa + 1;
+    const bool hb = sb < slices;
+    ray_unit_prep<M, TPL, LPC, MAXR>(
+        smem, blockIdx.x * LPC, V, N, sino + (size_t)sa * V * N, hb ? sino + (size_t)sb * V * N : nullptr,
+        pa.dark ? pa.dark + (size_t)sa * N : nullptr, (pa.dark && hb) ? pa.dark + (size_t)sb * N : nullptr,
+        pa.flat ? pa.flat + (size_t)sa * N : nullptr, (pa.flat && hb) ? pa.flat + (size_t)sb * N : nullptr, pa, mode,
+        g, two_alpha, Z + (size_t)pl * V * M, tw);
 }
 
 template <int M, int TPL, int CPC, int MAXR>
@@ -102,9 +120,10 @@ template <int M> struct FwdCfg {
 
 template <int M, int MAXR>
 bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int mode, const float* g, float* vol,
-                              void* ws, cudaStream_t st, int max_chunk, int lanes) {
+                              void* ws, cudaStream_t st, int max_chunk, int lanes, const PrepArgs* prep) {
     using C = FwdCfg<M>;
     static bool attr_ok = set_smem(k_ray_fft<M, C::TPL, C::LPC1, MAXR>, C::S1) &&
+                          set_smem(k_ray_fft_prep<M, C::TPL, C::LPC1, MAXR>, C::S1) &&
                           set_smem(k_grid_col<M, C::TPL, C::CPC, MAXR>, C::S2) &&
                           set_smem(k_row_ifft<M, C::TPL, C::TPC, MAXR>, C::S3);
     if (!attr_ok) return BST_ERR_CUDA;
@@ -133,8 +152,13 @@ bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int 
         float2* Z = (float2*)ws + (size_t)l * lane_elems;
         float2* T = Z + (size_t)chunk * V * M;
         bst_timing_mark(p, s, -1);
-        k_ray_fft<M, C::TPL, C::LPC1, MAXR><<<dim3((V + C::LPC1 - 1) / C::LPC1, np), C::TPL * C::LPC1, C::S1, s>>>(
-            sino, slices, p0, N, V, mode, g, two_alpha, Z, p->tw);
+        if (prep)
+            k_ray_fft_prep<M, C::TPL, C::LPC1, MAXR>
+                <<<dim3((V + C::LPC1 - 1) / C::LPC1, np), C::TPL * C::LPC1, C::S1, s>>>(
+                    sino, slices, p0, N, V, *prep, mode, g, two_alpha, Z, p->tw);
+        else
+            k_ray_fft<M, C::TPL, C::LPC1, MAXR><<<dim3((V + C::LPC1 - 1) / C::LPC1, np), C::TPL * C::LPC1, C::S1, s>>>(
+                sino, slices, p0, N, V, mode, g, two_alpha, Z, p->tw);
         bst_timing_mark(p, s, 0);
         k_grid_col<M, C::TPL, C::CPC, MAXR><<<dim3((M / 2 + C::CPC - 1) / C::CPC, np), C::TPL * C::CPC, C::S2, s>>>(
             Z, V, N, p->geo_J, p->geo_f, T, p->tw);
@@ -157,17 +181,32 @@ bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int 
 #define BST_FOR_EACH_M(X) \
     X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(48) X(96) X(192) X(384) X(768) X(1536) X(3072)
 
-bst_status_t bst_launch_forward_chunked(bst_plan_s* p, const float* sino, int slices, int mode, const float* g,
-                                        float* vol, void* ws, cudaStream_t st, int max_chunk, int lanes) {
+static bst_status_t forward_dispatch(bst_plan_s* p, const float* sino, int slices, int mode, const float* g,
+                                     float* vol, void* ws, cudaStream_t st, int max_chunk, int lanes,
+                                     const bst::PrepArgs* prep) {
     switch (p->M) {
-#define BST_CASE(m) \
-    case m:                                                                                              \
-        return p->maxr == 8 ? bst::launch_forward_M<m, 8>(p, sino, slices, mode, g, vol, ws, st, max_chunk, lanes) \
-                            : bst::launch_forward_M<m, 16>(p, sino, slices, mode, g, vol, ws, st, max_chunk, lanes);
+#define BST_CASE(m)                                                                                         \
+    case m:                                                                                                 \
+        return p->maxr == 8                                                                                 \
+                   ? bst::launch_forward_M<m, 8>(p, sino, slices, mode, g, vol, ws, st, max_chunk, lanes, prep) \
+                   : bst::launch_forward_M<m, 16>(p, sino, slices, mode, g, vol, ws, st, max_chunk, lanes, prep);
         BST_FOR_EACH_M(BST_CASE)
 #undef BST_CASE
     }
     return BST_ERR_UNSUPPORTED_SIZE;
+}
+
+bst_status_t bst_launch_forward_chunked(bst_plan_s* p, const float* sino, int slices, int mode, const float* g,
+                                        float* vol, void* ws, cudaStream_t st, int max_chunk, int lanes) {
+    return forward_dispatch(p, sino, slices, mode, g, vol, ws, st, max_chunk, lanes, nullptr);
+}
+
+bst_status_t bst_launch_forward_prep(bst_plan_s* p, const float* sino, int slices, const bst::PrepArgs& prep,
+                                     const float* g, float* vol, void* ws, size_t ws_bytes, cudaStream_t st) {
+    const int pairs = (slices + 1) / 2;
+    const int chunk = std::min(pairs, p->chunk_pairs);
+    const int lanes = ws_bytes >= 2 * (size_t)chunk * bsth::fwd_bytes_per_pair(p) ? 2 : 1;
+    return forward_dispatch(p, sino, slices, BSTK_FILTER, g, vol, ws, st, p->chunk_pairs, lanes, &prep);
 }
 
 bst_status_t bst_launch_forward(bst_plan_s* p, const float* sino, int slices, int mode, const float* g, float* vol,
@@ -212,4 +251,40 @@ bst_status_t bst_build_geo_table(bst_plan_s* p) {
     bst::k_geo_table<<<(unsigned)((n + 255) / 256), 256>>>(p->geo(), p->M, p->geo_J, p->geo_f);
     if (cudaGetLastError() != cudaSuccess) return BST_ERR_CUDA;
     return cudaDeviceSynchronize() == cudaSuccess ? BST_OK : BST_ERR_CUDA;
+}
+
+// I0(x) from its power series sum_k ((x/2)^(2k) / (k!)^2), in double
+static double bessel_i0(double x) {
+    double term = 1.0, sum = 1.0;
+    const double q = 0.25 * x * x;
+    for (int k = 1; k < 500 && term > 1e-18 * sum; ++k) {
+        term *= q / ((double)k * (double)k);
+        sum += term;
+    }
+    return sum;
+}
+
+extern "C" bst_status_t bst_fbp_prep(bst_plan_t p, const float* d_sino, int slices, const float* d_dark,
+                                     const float* d_flat, float shift, float kb_beta, float kb_halfwidth,
+                                     const float* d_g, float* d_volume, void* d_ws, size_t ws_bytes,
+                                     bst_stream_t stream) {
+    if (!p || !d_sino || !d_volume || slices <= 0) return BST_ERR_INVALID_ARGUMENT;
+    if (d_dark && !d_flat) return BST_ERR_INVALID_ARGUMENT;
+    if (!std::isfinite(shift) || std::fabs(shift) >= (float)p->N) return BST_ERR_INVALID_ARGUMENT;
+    if (!(kb_beta >= 0.f) || !std::isfinite(kb_beta) || (kb_beta > 0.f && !(kb_halfwidth > 0.f)))
+        return BST_ERR_INVALID_ARGUMENT;
+    const size_t ns = (size_t)slices * p->V * p->N * sizeof(float), nv = (size_t)slices * p->N * p->N * sizeof(float);
+    const uintptr_t a0 = (uintptr_t)d_sino, b0 = (uintptr_t)d_volume;
+    if (a0 < b0 + nv && b0 < a0 + ns) return BST_ERR_INVALID_ARGUMENT;
+    if (!d_ws || ws_bytes < bst_workspace_bytes(p, slices)) return BST_ERR_WORKSPACE_TOO_SMALL;
+    bst::PrepArgs pa;
+    pa.dark = d_dark;
+    pa.flat = d_flat;
+    pa.shift = shift;
+    pa.shift_int = (int)std::floor(shift);
+    pa.shift_frac = (float)((double)shift - std::floor((double)shift));
+    pa.kb_beta = kb_beta;
+    pa.kb_inv_half = kb_beta > 0.f ? 1.f / kb_halfwidth : 0.f;
+    pa.kb_norm = kb_beta > 0.f ? (float)(1.0 / bessel_i0((double)kb_beta)) : 1.f;
+    return bst_launch_forward_prep(p, d_sino, slices, pa, d_g, d_volume, d_ws, ws_bytes, (cudaStream_t)stream);
 }

@@ -127,3 +127,39 @@ def test_host_pipeline_matches_device_path(bst):
     ref = plan.fbp(h.cuda()).cpu()
     for s in (0, 1, 31, 32, 33, S - 1):
         assert_parity(out[s].numpy(), ref[s].numpy(), what=f"host path slice {s}")
+
+
+@pytest.mark.parametrize("case", ["counts", "shift", "window", "all"])
+def test_prep_stages_match_oracle(bst, case):
+    """bst_fbp_prep: normalization (Sec. 1 (a)), centering (Sec. 1 (b)) and the
+    P1 window against the oracle's prepared path."""
+    from oracle import prep
+    N, V, S = 128, 96, 3
+    rng = np.random.default_rng(17)
+    theta = synth.uniform_angles(V)
+    y = np.stack([synth.ellipse_sinogram(synth.random_ellipses(rng, fov_safe=True), theta, N) for _ in range(S)])
+    flat = rng.uniform(9000, 11000, (S, N))
+    dark = rng.uniform(50, 150, (S, N))
+    counts = (flat[:, None, :] - dark[:, None, :]) * np.exp(-y) + dark[:, None, :]
+    kw = {}
+    if case in ("counts", "all"):
+        sino, kw["flat"], kw["dark"] = counts, flat, dark
+    else:
+        sino = y
+    if case in ("shift", "all"):
+        kw["shift"] = -3.62
+    if case in ("window", "all"):
+        kw["kb_beta"], kw["kb_halfwidth"] = 3.0, 0.95
+    plan = bst.Plan(N, theta, 2)
+    d = {k: torch.from_numpy(np.asarray(v, dtype=np.float32)).cuda() if isinstance(v, np.ndarray) else v
+         for k, v in kw.items()}
+    got = plan.fbp_prep(torch.from_numpy(sino.astype(np.float32)).cuda(), **d).cpu().numpy()
+    for s in range(S):
+        okw = dict(kw)
+        if "flat" in okw:
+            okw["flat"] = np.asarray(okw["flat"][s], dtype=np.float32).astype(np.float64)
+            okw["dark"] = np.asarray(okw["dark"][s], dtype=np.float32).astype(np.float64)
+        if "kb_halfwidth" in okw:
+            okw["kb_half"] = okw.pop("kb_halfwidth")
+        ref = prep.prepared_fbp(sino[s].astype(np.float32).astype(np.float64), theta, **okw)
+        assert_parity(got[s], ref, what=f"prep {case} slice {s}")
