@@ -25,10 +25,11 @@ struct bst_plan_s {
     float2* cs32 = nullptr;         // [V] (cos, sin) in float, slant-stack tile offsets
     float* wq = nullptr;            // [V] trapezoid weights of Eq. 2
     int* err = nullptr;             // sticky device error word
-    // angular part of the gridding geometry of the half grid c' in [0, M/2):
-    // bracket J (-2: point is zero) and fraction, [M/2][M], built at plan creation
-    short* geo_J = nullptr;
-    float* geo_f = nullptr;
+    // gridding geometry of the half grid c' in [0, M/2), [M/2][M], built at plan
+    // creation: (bracket J << 16) | floor(rho) (J = -2: the point is zero) and
+    // (angle fraction, radius fraction)
+    int* geo_J = nullptr;
+    float2* geo_f = nullptr;
     int chunk_pairs = 1;            // slice pairs per chunk of the forward path
     int maxr = 16;                  // FFT radix schedule of the forward path (16 or 8; autotuned)
     // two plan-owned streams that alternate chunks of the forward path (fork

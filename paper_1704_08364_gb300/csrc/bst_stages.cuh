@@ -82,7 +82,7 @@ struct ColDst {
 // Two points per step; all eight tap loads are issued before any is used.
 template <int M, int TPL, int PPT>
 __device__ __forceinline__ void gather_side(const float2* __restrict__ Zp, int V, int q, bool live, int t,
-                                            const short* __restrict__ gJq, const float* __restrict__ gFq,
+                                            const int* __restrict__ gJq, const float2* __restrict__ gFq,
                                             bool mirror, const SmemLine& sm) {
     constexpr int H = M >> 1;
     const float2 zero = make_float2(0.f, 0.f);
@@ -94,16 +94,15 @@ __device__ __forceinline__ void gather_side(const float2* __restrict__ Zp, int V
         for (int u = 0; u < 2; ++u) {
             const int ridx = t + (i + u) * TPL;
             const int ry = signed_freq(ridx, M);
-            const int Jt = __ldg(gJq + ridx);
-            wt[u] = __ldg(gFq + ridx);
+            // the plan's table: bracket and floor(rho) packed, angle and radius fractions
+            const int jk = __ldg(gJq + ridx);
+            const float2 fw = __ldg(gFq + ridx);
+            const int Jt = jk >> 16;
+            const int k0 = jk & 0xffff;
+            const float frac = fw.y;
+            wt[u] = fw.x;
             // a table bracket >= -1 means the point is inside the band and not the origin
             const bool ok = live && Jt >= -1;
-            const int rho2 = q * q + ry * ry;
-            const float rf = __fsqrt_rn((float)rho2);
-            int k0 = (int)rf;
-            if (k0 * k0 > rho2) --k0;
-            else if ((k0 + 1) * (k0 + 1) <= rho2) ++k0;
-            const float frac = __fdividef((float)(rho2 - k0 * k0), rf + (float)k0);
             // kappa = +rho for q >= 0 when r' >= 0; the mirror point has -kappa
             const bool plus = (ry >= 0) != mirror;
             int K0;
@@ -313,7 +312,7 @@ __device__ __forceinline__ void ray_unit(float2* smem, int j0, int V, int N, con
 // fall on neighbouring polar samples.
 template <int M, int TPL, int CPC, int MAXR>
 __device__ __forceinline__ void grid_unit(float2* smem, int q0, int V, int N, const float2* __restrict__ Zp,
-                                          const short* __restrict__ gJ, const float* __restrict__ gF,
+                                          const int* __restrict__ gJ, const float2* __restrict__ gF,
                                           float2* __restrict__ Tp, const float2* __restrict__ tw) {
     constexpr int PPT = M / TPL;   // Cartesian points per thread and column
     static_assert(PPT % 2 == 0, "points per thread");
@@ -322,8 +321,8 @@ __device__ __forceinline__ void grid_unit(float2* smem, int q0, int V, int N, co
     const int q = q0 + cp;
     const bool live = q < (M >> 1);
     const SmemLine sm{smem + cp * smem_line_len(M)};
-    const short* gJq = gJ + (size_t)(live ? q : 0) * M;
-    const float* gFq = gF + (size_t)(live ? q : 0) * M;
+    const int* gJq = gJ + (size_t)(live ? q : 0) * M;
+    const float2* gFq = gF + (size_t)(live ? q : 0) * M;
 #pragma unroll 1
     for (int side = 0; side < 2; ++side) {
         if (side == 0 || q != 0) {

@@ -45,19 +45,19 @@ __global__ void __launch_bounds__(TPL * LPC)
 // Plan set-up: the angular part of the geometry of every point (q, r') of the
 // half grid q in [0, M/2) (the mirror half shares it), bracket -2 for points
 // that are zero (outside the band, or the origin, which takes the DC mean).
-__global__ void k_geo_table(Geo geo, int M, short* __restrict__ gJ, float* __restrict__ gF) {
+__global__ void k_geo_table(Geo geo, int M, int* __restrict__ gJ, float2* __restrict__ gF) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)(M / 2) * M) return;
     const int q = (int)(idx / M), ridx = (int)(idx % M);
     const int ry = signed_freq(ridx, M);
     Polar P;
-    short J = -2;
-    float f = 0.f;
+    int jk = (int)(-2 * 65536);
+    float2 f = make_float2(0.f, 0.f);
     if (!(q == 0 && ry == 0) && polar_of(q, ry, geo, P)) {
-        J = (short)P.J;
-        f = P.fth;
+        jk = P.J * 65536 + P.k0;
+        f = make_float2(P.fth, P.frac);
     }
-    gJ[idx] = J;
+    gJ[idx] = jk;
     gF[idx] = f;
 }
 
@@ -79,8 +79,8 @@ __global__ void __launch_bounds__(TPL * LPC)
 
 template <int M, int TPL, int CPC, int MAXR>
 __global__ void __launch_bounds__(TPL * CPC, (TPL * CPC <= 256) ? 1024 / (TPL * CPC) : 1)
-    k_grid_col(const float2* __restrict__ Z, int V, int N, const short* __restrict__ gJ,
-               const float* __restrict__ gF, float2* __restrict__ T, const float2* __restrict__ tw) {
+    k_grid_col(const float2* __restrict__ Z, int V, int N, const int* __restrict__ gJ,
+               const float2* __restrict__ gF, float2* __restrict__ T, const float2* __restrict__ tw) {
     extern __shared__ float2 smem[];
     const int pl = blockIdx.y;
     grid_unit<M, TPL, CPC, MAXR>(smem, blockIdx.x * CPC, V, N, Z + (size_t)pl * V * M, gJ, gF,
@@ -246,8 +246,8 @@ bst_status_t bst_launch_ray_spectrum(bst_plan_s* p, const float* sino, int slice
 
 bst_status_t bst_build_geo_table(bst_plan_s* p) {
     const size_t n = (size_t)(p->M / 2) * p->M;
-    if (cudaMalloc((void**)&p->geo_J, n * sizeof(short)) != cudaSuccess) return BST_ERR_OUT_OF_MEMORY;
-    if (cudaMalloc((void**)&p->geo_f, n * sizeof(float)) != cudaSuccess) return BST_ERR_OUT_OF_MEMORY;
+    if (cudaMalloc((void**)&p->geo_J, n * sizeof(int)) != cudaSuccess) return BST_ERR_OUT_OF_MEMORY;
+    if (cudaMalloc((void**)&p->geo_f, n * sizeof(float2)) != cudaSuccess) return BST_ERR_OUT_OF_MEMORY;
     bst::k_geo_table<<<(unsigned)((n + 255) / 256), 256>>>(p->geo(), p->M, p->geo_J, p->geo_f);
     if (cudaGetLastError() != cudaSuccess) return BST_ERR_CUDA;
     return cudaDeviceSynchronize() == cudaSuccess ? BST_OK : BST_ERR_CUDA;

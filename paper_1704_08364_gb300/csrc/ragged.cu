@@ -35,8 +35,8 @@ struct RItem {
     float2* Z;        // [V][M]
     float2* T;        // [ceil(N/4)][M][4]
     const float2* tw;
-    const short* gJ;
-    const float* gF;
+    const int* gJ;
+    const float2* gF;
     int M, N, V, maxr;
     float scale, two_alpha;
     int n[3];         // units per stage
