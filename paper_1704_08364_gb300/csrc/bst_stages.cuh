@@ -86,17 +86,39 @@ __device__ __forceinline__ void gather_side(const float2* __restrict__ Zp, int V
                                             bool mirror, const SmemLine& sm) {
     constexpr int H = M >> 1;
     const float2 zero = make_float2(0.f, 0.f);
+    // the plan's table (bracket and floor(rho) packed; angle and radius
+    // fractions), prefetched one step ahead so that each step waits on the tap
+    // loads only
+    int jn[4];
+    float2 fn[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        jn[u] = __ldg(gJq + t + (u < PPT ? u : 0) * TPL);
+        fn[u] = __ldg(gFq + t + (u < PPT ? u : 0) * TPL);
+    }
 #pragma unroll 1
     for (int i = 0; i < PPT; i += 2) {
         float2 z[2][4];
         float wk[2], wt[2];
+        const int jc[2] = {jn[0], jn[1]};
+        const float2 fc[2] = {fn[0], fn[1]};
+        jn[0] = jn[2];
+        jn[1] = jn[3];
+        fn[0] = fn[2];
+        fn[1] = fn[3];
+        if (i + 4 < PPT) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                jn[2 + u] = __ldg(gJq + t + (i + 4 + u) * TPL);
+                fn[2 + u] = __ldg(gFq + t + (i + 4 + u) * TPL);
+            }
+        }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const int ridx = t + (i + u) * TPL;
             const int ry = signed_freq(ridx, M);
-            // the plan's table: bracket and floor(rho) packed, angle and radius fractions
-            const int jk = __ldg(gJq + ridx);
-            const float2 fw = __ldg(gFq + ridx);
+            const int jk = jc[u];
+            const float2 fw = fc[u];
             const int Jt = jk >> 16;
             const int k0 = jk & 0xffff;
             const float frac = fw.y;
