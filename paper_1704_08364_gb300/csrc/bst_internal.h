@@ -34,9 +34,9 @@ struct bst_plan_s {
     int maxr = 16;                  // FFT radix schedule of the forward path (16 or 8; autotuned)
     // two plan-owned streams that alternate chunks of the forward path (fork
     // from and join back to the caller's stream with events), created on first use
-    cudaStream_t lane[2] = {nullptr, nullptr};
+    cudaStream_t lane[3] = {nullptr, nullptr, nullptr};
     cudaEvent_t ev_fork = nullptr;
-    cudaEvent_t ev_join[2] = {nullptr, nullptr};
+    cudaEvent_t ev_join[3] = {nullptr, nullptr, nullptr};
     // bst_fbp_host: upload and download streams and their events, created on first use
     cudaStream_t hs[2] = {nullptr, nullptr};
     cudaEvent_t hev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -71,6 +71,10 @@ struct bst_plan_s {
 };
 
 namespace bsth {
+
+// chunks of the forward path in flight at once, each on its own stream with its
+// own workspace (a third one measured no faster than two at 2048^3)
+constexpr int kMaxLanes = 2;
 
 inline bool supported_fft_length(int M) {
     int m = M;

@@ -131,24 +131,25 @@ bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int 
     const int pairs = (slices + 1) / 2;
     const int chunk = std::min(pairs, max_chunk);
     const int nchunks = (pairs + chunk - 1) / chunk;
-    // chunks alternate between two streams (each with its own half of the
+    // chunks rotate over up to kMaxLanes streams (each with its own part of the
     // workspace) so that one chunk's gridding overlaps the next chunk's FFTs;
     // per-stage timing keeps everything on the caller's stream
-    const int nl = (lanes >= 2 && nchunks >= 2 && !p->timing && bst_ensure_lanes(p)) ? 2 : 1;
+    int nl = std::min(std::min(lanes, nchunks), bsth::kMaxLanes);
+    if (nl < 2 || p->timing || !bst_ensure_lanes(p)) nl = 1;
     const size_t lane_elems = (size_t)chunk * (V + (size_t)((N + 3) / 4) * 4) * M;
     const float scale = (float)((double)N / (2.0 * (double)M * (double)M));
     const float two_alpha = (float)(2 * p->alpha);
     const int row_tiles = (N + 3) / 4;
-    if (nl == 2) {
+    if (nl > 1) {
         if (cudaEventRecord(p->ev_fork, st) != cudaSuccess) return BST_ERR_CUDA;
-        for (int l = 0; l < 2; ++l)
+        for (int l = 0; l < nl; ++l)
             if (cudaStreamWaitEvent(p->lane[l], p->ev_fork, 0) != cudaSuccess) return BST_ERR_CUDA;
     }
     for (int c = 0; c < nchunks; ++c) {
         const int p0 = c * chunk;
         const int np = std::min(chunk, pairs - p0);
         const int l = c % nl;
-        cudaStream_t s = nl == 2 ? p->lane[l] : st;
+        cudaStream_t s = nl > 1 ? p->lane[l] : st;
         float2* Z = (float2*)ws + (size_t)l * lane_elems;
         float2* T = Z + (size_t)chunk * V * M;
         bst_timing_mark(p, s, -1);
@@ -167,8 +168,8 @@ bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int 
             T, slices, p0, N, scale, vol, p->tw);
         bst_timing_mark(p, s, 2);
     }
-    if (nl == 2) {
-        for (int l = 0; l < 2; ++l) {
+    if (nl > 1) {
+        for (int l = 0; l < nl; ++l) {
             if (cudaEventRecord(p->ev_join[l], p->lane[l]) != cudaSuccess) return BST_ERR_CUDA;
             if (cudaStreamWaitEvent(st, p->ev_join[l], 0) != cudaSuccess) return BST_ERR_CUDA;
         }
@@ -205,7 +206,7 @@ bst_status_t bst_launch_forward_prep(bst_plan_s* p, const float* sino, int slice
                                      const float* g, float* vol, void* ws, size_t ws_bytes, cudaStream_t st) {
     const int pairs = (slices + 1) / 2;
     const int chunk = std::min(pairs, p->chunk_pairs);
-    const int lanes = ws_bytes >= 2 * (size_t)chunk * bsth::fwd_bytes_per_pair(p) ? 2 : 1;
+    const int lanes = (int)std::min<size_t>(bsth::kMaxLanes, ws_bytes / ((size_t)chunk * bsth::fwd_bytes_per_pair(p)));
     return forward_dispatch(p, sino, slices, BSTK_FILTER, g, vol, ws, st, p->chunk_pairs, lanes, &prep);
 }
 
@@ -213,7 +214,7 @@ bst_status_t bst_launch_forward(bst_plan_s* p, const float* sino, int slices, in
                                 void* ws, size_t ws_bytes, cudaStream_t st) {
     const int pairs = (slices + 1) / 2;
     const int chunk = std::min(pairs, p->chunk_pairs);
-    const int lanes = ws_bytes >= 2 * (size_t)chunk * bsth::fwd_bytes_per_pair(p) ? 2 : 1;
+    const int lanes = (int)std::min<size_t>(bsth::kMaxLanes, ws_bytes / ((size_t)chunk * bsth::fwd_bytes_per_pair(p)));
     return bst_launch_forward_chunked(p, sino, slices, mode, g, vol, ws, st, p->chunk_pairs, lanes);
 }
 

@@ -24,7 +24,7 @@ bool upload(T** dptr, const std::vector<T>& host) {
 void free_plan(bst_plan_s* p) {
     if (!p) return;
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < bsth::kMaxLanes; ++i) {
         if (p->lane[i]) cudaStreamDestroy(p->lane[i]);
         if (p->ev_join[i]) cudaEventDestroy(p->ev_join[i]);
     }
@@ -62,8 +62,8 @@ bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
 }  // namespace
 
 bool bst_ensure_lanes(bst_plan_s* p) {
-    if (p->lane[0] && p->lane[1]) return true;
-    for (int i = 0; i < 2; ++i) {
+    if (p->lane[bsth::kMaxLanes - 1]) return true;
+    for (int i = 0; i < bsth::kMaxLanes; ++i) {
         if (!p->lane[i] && cudaStreamCreateWithFlags(&p->lane[i], cudaStreamNonBlocking) != cudaSuccess) return false;
         if (!p->ev_join[i] && cudaEventCreateWithFlags(&p->ev_join[i], cudaEventDisableTiming) != cudaSuccess)
             return false;
@@ -238,7 +238,8 @@ size_t bst_workspace_bytes(bst_plan_t p, int slices) {
     if (!p || slices <= 0) return 0;
     const int pairs = (slices + 1) / 2;
     const int chunk = std::min(pairs, p->chunk_pairs);
-    const int lanes = pairs > chunk ? 2 : 1;   // two chunks in flight when there is more than one
+    const int nchunks = (pairs + chunk - 1) / chunk;
+    const int lanes = std::min(nchunks, bsth::kMaxLanes);   // chunks in flight at once
     return (size_t)lanes * chunk * bsth::fwd_bytes_per_pair(p);
 }
 
