@@ -87,8 +87,8 @@ __device__ __forceinline__ void gather_side(const float2* __restrict__ Zp, int V
     constexpr int H = M >> 1;
     const float2 zero = make_float2(0.f, 0.f);
     // the plan's table (bracket and floor(rho) packed; angle and radius
-    // fractions), prefetched one step ahead so that each step waits on the tap
-    // loads only
+    // fractions), prefetched two steps ahead so that each step waits on the
+    // tap loads only
     int jn[4];
     float2 fn[4];
 #pragma unroll
