@@ -16,6 +16,11 @@ bst      The BST method of Sec. 2 (Theorem 2.1, Eq. 3) step by step in the
          along rays, the filter / 1/sigma weight, polar-to-Cartesian bilinear
          gridding in the Fourier domain, 2D inverse FFT, crop (fftshift) and
          scale.  A direct-DFT mode replaces the FFTs by explicit sums.
+kb       Stage P5 as Kaiser-Bessel convolution gridding (polar samples weighted
+         by their cell area, spread with a separable KB kernel, inverse FFT,
+         division by the kernel's transform), and the direct sum over polar
+         samples that it approximates.
+prep     The pre-reconstruction stages: normalization, centering, window P1.
 adjoint  The exact adjoint of the discrete BST operator (a Fourier-slice
          projector, the "FST" dual of Sec. 2) and the gradient of
          ||FBP(p; g) - f||^2 with respect to the filter taps g.
