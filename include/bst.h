@@ -21,8 +21,9 @@
  *     float32, device memory owned by the caller; the library never frees or
  *     retains caller pointers;
  *   - the ordinary-frequency Fourier convention, so Eq. 3 holds with
- *     constant 1; bilinear interpolation in (signed radius, angle); the
- *     Nyquist bin is zero; the DC bin is averaged over angles.
+ *     constant 1; bilinear interpolation in (signed radius, angle) by default
+ *     (Kaiser-Bessel gridding on request, bst_plan_set_gridding); the Nyquist
+ *     bin is zero; the DC bin is averaged over angles (bilinear).
  *
  * Every call is asynchronous on the given stream.  The returned status
  * covers argument validation and launch errors only; errors detected on the
@@ -52,6 +53,12 @@ typedef enum {
     BST_W_FILTER = 0,      /* FBP: P4 weight W[k] = g[k] (g = NULL: ramp, g = 1) */
     BST_W_BACKPROJECT = 1  /* plain B: W[k] = 1/sigma_k = M dt / k, W[0] = 0 */
 } bst_mode_t;
+
+/* Interpolation kernel of stage P5 (Sec. 2 names the step, not the kernel). */
+typedef enum {
+    BST_GRID_BILINEAR = 0,      /* bilinear in (signed radius, angle), gather form */
+    BST_GRID_KAISER_BESSEL = 1  /* KB convolution gridding with deapodization */
+} bst_gridding_t;
 
 typedef struct bst_plan_s* bst_plan_t;
 typedef void* bst_stream_t;   /* a cudaStream_t; NULL is the legacy default stream */
@@ -126,7 +133,8 @@ size_t bst_adjoint_workspace_bytes(bst_plan_t plan, int slices);
  *   d_volume [slices][N][N] -> d_sino [slices][V][N], device float32.
  * The first call builds the plan's cell lists of the gridding (device
  * memory owned by the plan); it synchronises the stream.
- * Errors: INVALID_ARGUMENT, WORKSPACE_TOO_SMALL, CUDA, OUT_OF_MEMORY. */
+ * Errors: INVALID_ARGUMENT (also for a plan with KB gridding),
+ * WORKSPACE_TOO_SMALL, CUDA, OUT_OF_MEMORY. */
 bst_status_t radon_adjoint(bst_plan_t plan, bst_mode_t mode, const float* d_g,
                            const float* d_volume, int slices, float* d_sino,
                            void* d_ws, size_t ws_bytes, bst_stream_t stream);
@@ -137,7 +145,8 @@ bst_status_t radon_adjoint(bst_plan_t plan, bst_mode_t mode, const float* d_g,
  *                 Re(conj(lambda_j[k]) * Y_j[k]),
  * Y = dt * DFT of the padded rays, lambda = grad_vol pulled back through the
  * crop, 2D transform, gridding and DC mean.  Deterministic (fixed reduction
- * order).  d_grad_g is overwritten.  Workspace: bst_adjoint_workspace_bytes. */
+ * order).  d_grad_g is overwritten.  Workspace: bst_adjoint_workspace_bytes.
+ * A plan with KB gridding is rejected (INVALID_ARGUMENT). */
 bst_status_t bst_fbp_filter_grad(bst_plan_t plan, const float* d_sino,
                                  const float* d_grad_vol, int slices,
                                  float* d_grad_g, void* d_ws, size_t ws_bytes,
@@ -205,6 +214,34 @@ bst_status_t bst_fbp_host(bst_plan_t plan, const float* h_sino, int slices,
 bst_status_t bst_plan_set_schedule(bst_plan_t plan, int max_radix);
 int bst_plan_get_schedule(bst_plan_t plan);
 
+/* Interpolation kernel of stage P5 for bst_fbp, bst_backproject,
+ * bst_fbp_prep, bst_fbp_host and bst_fbp_noalloc on this plan.
+ *   BST_GRID_BILINEAR (width ignored): the default.
+ *   BST_GRID_KAISER_BESSEL, width W in {2, 4, 6, 8} bins: classical
+ *     convolution gridding.  Each polar sample Y_j[k] of P3, times the P4
+ *     weight, is given the area of its polar cell dtheta_j |sigma_k| dsigma
+ *     (dsigma / 4 for the DC cell; dtheta_j the trapezoid weights on the half
+ *     circle), spread onto the Cartesian frequency grid with the separable
+ *     kernel phi(x) = (I0(beta sqrt(1 - (2x/W)^2)) - 1) / (I0(beta) - 1) (KB
+ *     without its pedestal) over the W points x in (-W/2, W/2] of each axis,
+ *     beta =
+ *     pi sqrt((W / alpha)^2 (alpha - 1/2)^2 - 0.8), and after the 2D inverse
+ *     FFT each pixel is divided by C(c_p / M) C(r_p / M), C the Fourier
+ *     transform of phi.  The result approximates the direct polar sum
+ *     sum_{j,k} a_jk exp(2 pi i omega_jk . u) (relative error ~3e-6 at W = 6,
+ *     alpha = 2), which bilinear interpolation reaches only to ~1e-1.  At
+ *     alpha = 1 the grid has no guard band: accurate inside the inscribed
+ *     disk, ill-conditioned (deapodization gain up to ~1e7) at the edge.
+ * Builds the plan's KB tables (a kernel table, the deapodization and, per
+ * strip of Cartesian columns, the list of samples whose footprint touches
+ * it: about 4 (1 + (W + 2) / CS) V M bytes) synchronously; synchronises the
+ * device.  radon_adjoint, bst_fbp_filter_grad and the ragged batch need a
+ * bilinear plan and reject a KB one.  Errors: INVALID_ARGUMENT (kind, width),
+ * OUT_OF_MEMORY, CUDA (the plan then stays bilinear). */
+bst_status_t bst_plan_set_gridding(bst_plan_t plan, int kind, int width);
+/* The plan's gridding kind and width (2 for bilinear). Errors: INVALID_ARGUMENT. */
+bst_status_t bst_plan_get_gridding(bst_plan_t plan, int* kind, int* width);
+
 /* Autotuner: time the plan's forward path on a synthetic batch of about
  * 256 MiB (`slices` slices; <= 0 picks that size) with each radix schedule,
  * keep the faster one and return it in *chosen.  Allocates and frees its own
@@ -230,7 +267,8 @@ int bst_ragged_pair_items(bst_ragged_t batch);
  * uploads the work queue; drops a captured graph.  flags: 0; bit 0 is a
  * diagnostic that leaves the ray stage of the first pair-item unqueued, so
  * that its dependent units wait until the spin limit and the launch reports
- * BST_ERR_TIMEOUT (used to test the bounded waits). */
+ * BST_ERR_TIMEOUT (used to test the bounded waits).  Every plan must use
+ * bilinear gridding (INVALID_ARGUMENT otherwise). */
 bst_status_t bst_ragged_bind(bst_ragged_t batch, const float* const* d_sinos, const float* const* d_g,
                              float* const* d_volumes, void* d_ws, size_t ws_bytes, int flags);
 /* Iterations (each with a ~256 ns sleep) a dependency wait may spin before it

@@ -24,7 +24,7 @@ approximates).  ``kb_fbp`` approximates it in O(M^2 log M):
 
     1. spread: G[r', c'] = sum_s a_s phi(c' - c_s) phi(r' - r_s) on the
        M-periodic grid, phi the KB kernel of width W (in bins) normalised to
-       phi(0) = 1, support c' - c_s in (-W/2, W/2];
+       phi(0) = 1, over the W points c' - c_s in (-W/2, W/2];
     2. x_pad[r_p, c_p] = sum G[r', c'] exp(+2 pi i (r' r_p + c' c_p) / M);
     3. volume[r][c] = Re x_pad / (C(c_p / M) C(r_p / M)), C the continuous
        Fourier transform of phi (deapodization).
@@ -32,7 +32,14 @@ approximates).  ``kb_fbp`` approximates it in O(M^2 log M):
 Readings (the paper gives no kernel): W = 6 by default; shape
 beta = pi sqrt((W / alpha)^2 (alpha - 1/2)^2 - 0.8) with alpha = M / N the
 grid oversampling (the choice of Beatty, Nishimura and Pauly, 2005);
-phi(x) = I0(beta sqrt(1 - (2x/W)^2)) / I0(beta) for |x| <= W/2.
+phi(x) = (I0(beta sqrt(1 - (2x/W)^2)) - 1) / (I0(beta) - 1) for |x| <= W/2,
+the KB kernel with its pedestal removed.  The pedestal-free form is zero at
+the edge of the support, so a sample whose footprint edge falls exactly on a
+grid point (every sample at theta = 0 or pi/2 does) adds nothing there; the
+plain KB kernel, 1/I0(beta) at the edge, would make the gridded spectrum of a
+real slice depart from Hermitian symmetry by that much at each such tie
+(the half-open support keeps one edge point of a sample and drops the
+mirrored point of its mirror sample).
 """
 from __future__ import annotations
 
@@ -48,23 +55,28 @@ def kb_beta(width: int, pad_factor: float) -> float:
 
 
 def kb_kernel(x, width: int, beta: float) -> np.ndarray:
-    """phi(x) = I0(beta sqrt(1 - (2x/W)^2)) / I0(beta) on |x| <= W/2, else 0."""
+    """phi(x) = (I0(beta sqrt(1 - (2x/W)^2)) - 1) / (I0(beta) - 1) on |x| <= W/2,
+    else 0: the KB kernel without its pedestal, so phi(+-W/2) = 0."""
     x = np.asarray(x, dtype=np.float64)
     u = 2.0 * x / width
     inside = np.abs(u) <= 1.0
-    return np.where(inside, np.i0(beta * np.sqrt(np.maximum(1.0 - u * u, 0.0))) / np.i0(beta), 0.0)
+    v = (np.i0(beta * np.sqrt(np.maximum(1.0 - u * u, 0.0))) - 1.0) / (np.i0(beta) - 1.0)
+    return np.where(inside, v, 0.0)
 
 
 def kb_transform(nu, width: int, beta: float) -> np.ndarray:
-    """C(nu) = int phi(x) exp(-2 pi i nu x) dx = W sinh(z) / (z I0(beta)),
-    z = sqrt(beta^2 - (pi W nu)^2) (sin(|z|)/|z| when z is imaginary)."""
+    """C(nu) = int phi(x) exp(-2 pi i nu x) dx
+             = W (sinh(z) / z - sinc(W nu)) / (I0(beta) - 1),
+    z = sqrt(beta^2 - (pi W nu)^2) (sin(|z|)/|z| when z is imaginary),
+    sinc(x) = sin(pi x) / (pi x): the transform of I0(beta sqrt(1 - (2x/W)^2))
+    minus that of the pedestal 1 on [-W/2, W/2]."""
     nu = np.asarray(nu, dtype=np.float64)
     z2 = beta * beta - (np.pi * width * nu) ** 2
     z = np.sqrt(np.abs(z2))
     small = z < 1e-8
     zs = np.where(small, 1.0, z)
-    ratio = np.where(z2 >= 0, np.sinh(zs) / zs, np.sin(zs) / zs)
-    return width * np.where(small, 1.0, ratio) / np.i0(beta)
+    ratio = np.where(small, 1.0, np.where(z2 >= 0, np.sinh(zs) / zs, np.sin(zs) / zs))
+    return width * (ratio - np.sinc(width * nu)) / (np.i0(beta) - 1.0)
 
 
 def sample_weights(M: int, N: int, angles, mode: str = ob.FILTER, g=None) -> np.ndarray:
@@ -123,25 +135,27 @@ def direct_sum(y, angles, pad_factor: int = 2, mode: str = ob.FILTER, g=None, pi
 def spread(a, cs, rs, M: int, width: int, beta: float) -> np.ndarray:
     """Step 1: G[r' mod M, c' mod M] += a phi(c' - c_s) phi(r' - r_s) for the W
     grid points c' - c_s in (-W/2, W/2] of each axis."""
-    G = np.zeros((M, M), dtype=np.complex128)
+    G = np.zeros(M * M, dtype=np.complex128)
     c0 = np.floor(cs - width / 2.0).astype(np.int64) + 1
     r0 = np.floor(rs - width / 2.0).astype(np.int64) + 1
     for dc in range(width):
         wc = kb_kernel(c0 + dc - cs, width, beta)
         for dr in range(width):
-            wr = kb_kernel(r0 + dr - rs, width, beta)
-            np.add.at(G, ((r0 + dr) % M, (c0 + dc) % M), a * wc * wr)
-    return G
+            v = a * wc * kb_kernel(r0 + dr - rs, width, beta)
+            idx = ((r0 + dr) % M) * M + (c0 + dc) % M
+            G += np.bincount(idx, weights=v.real, minlength=M * M) + 1j * np.bincount(idx, weights=v.imag,
+                                                                                       minlength=M * M)
+    return G.reshape(M, M)
 
 
-def kb_fbp(y, angles, pad_factor: int = 2, mode: str = ob.FILTER, g=None, width: int = 6,
-           beta: float | None = None) -> np.ndarray:
-    """BST FBP (or plain B) of one sinogram y[V][N] with KB gridding in P5."""
-    y = np.asarray(y, dtype=np.float64)
-    N = y.shape[1]
-    M = pad_factor * N
-    beta = kb_beta(width, pad_factor) if beta is None else beta
-    a, cs, rs = weighted_samples(y, angles, pad_factor, mode, g)
+def kb_from_spectrum(Y, angles, N: int, mode: str = ob.FILTER, g=None, width: int = 6,
+                     beta: float | None = None) -> np.ndarray:
+    """Steps P4 (weight and cell area), P5 (KB spread), P6 and deapodization,
+    from the P3 spectrum Y[V][M]."""
+    M = Y.shape[-1]
+    beta = kb_beta(width, M / N) if beta is None else beta
+    a = (Y * sample_weights(M, N, angles, mode, g)).reshape(-1)
+    cs, rs = (v.reshape(-1) for v in sample_positions(M, angles))
     keep = a != 0
     G = spread(a[keep], cs[keep], rs[keep], M, width, beta)      # P5
     xp = (M * M) * np.fft.ifft2(G)                                # P6
@@ -149,3 +163,12 @@ def kb_fbp(y, angles, pad_factor: int = 2, mode: str = ob.FILTER, g=None, width:
     idx = p % M                                                   # P7 (fftshift in the indices)
     C = kb_transform(p / M, width, beta)
     return np.real(xp[np.ix_(idx, idx)]) / (C[:, None] * C[None, :])
+
+
+def kb_fbp(y, angles, pad_factor: int = 2, mode: str = ob.FILTER, g=None, width: int = 6,
+           beta: float | None = None) -> np.ndarray:
+    """BST FBP (or plain B) of one sinogram y[V][N] with KB gridding in P5."""
+    y = np.asarray(y, dtype=np.float64)
+    N = y.shape[1]
+    Y = ob.ray_spectrum(y, pad_factor * N)                        # P2, P3
+    return kb_from_spectrum(Y, angles, N, mode, g, width, beta)

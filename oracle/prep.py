@@ -45,11 +45,12 @@ def kaiser_bessel(t, beta: float, half: float) -> np.ndarray:
 
 
 def prepared_fbp(sino, angles, pad_factor: int = 2, g=None, flat=None, dark=None, shift: float = 0.0,
-                 kb_beta: float = 0.0, kb_half: float = 1.0, mode: str = ob.FILTER):
+                 kb_beta: float = 0.0, kb_half: float = 1.0, mode: str = ob.FILTER, grid_width: int = 0):
     """BST FBP of one slice after the pre-reconstruction stages.
 
     sino: counts [V][N] when ``flat`` (I0, broadcast to [V][N]) is given, else y.
-    ``flat``/``dark`` may be per-detector [N] rows (one slice's detector row)."""
+    ``flat``/``dark`` may be per-detector [N] rows (one slice's detector row).
+    grid_width > 0: stage P5 by Kaiser-Bessel gridding of that width (oracle.kb)."""
     s = np.asarray(sino, dtype=np.float64)
     V, N = s.shape
     M = pad_factor * N
@@ -60,4 +61,7 @@ def prepared_fbp(sino, angles, pad_factor: int = 2, g=None, flat=None, dark=None
     Y = ob.ray_spectrum(y, M)
     if shift != 0.0:
         Y = Y * np.exp(2j * np.pi * ob.signed_index(M) * shift / M)[None, :]
+    if grid_width > 0:
+        from . import kb
+        return kb.kb_from_spectrum(Y, angles, N, mode, g, grid_width)
     return ob.bst_from_spectrum(Y, angles, N, mode, g)

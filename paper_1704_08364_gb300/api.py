@@ -16,6 +16,8 @@ from . import _lib
 
 FILTER = 0
 BACKPROJECT = 1
+GRID_BILINEAR = 0
+GRID_KAISER_BESSEL = 1
 
 
 class BstError(RuntimeError):
@@ -107,6 +109,21 @@ class Plan:
     def schedule(self, max_radix: int):
         _check(self._lib.bst_plan_set_schedule(self._h, int(max_radix)), "bst_plan_set_schedule")
 
+    @property
+    def gridding(self) -> tuple[str, int]:
+        """Interpolation kernel of stage P5: ("bilinear", 2) or ("kaiser-bessel", W)."""
+        kind, width = ctypes.c_int(0), ctypes.c_int(0)
+        _check(self._lib.bst_plan_get_gridding(self._h, ctypes.byref(kind), ctypes.byref(width)),
+               "bst_plan_get_gridding")
+        return ("kaiser-bessel" if kind.value == GRID_KAISER_BESSEL else "bilinear", int(width.value))
+
+    def set_gridding(self, kind: str = "bilinear", width: int = 6):
+        """Select bilinear interpolation or Kaiser-Bessel gridding of width W bins
+        (bst_plan_set_gridding; builds the KB tables, synchronises the device)."""
+        k = {"bilinear": GRID_BILINEAR, "kaiser-bessel": GRID_KAISER_BESSEL, "kb": GRID_KAISER_BESSEL}[kind]
+        _check(self._lib.bst_plan_set_gridding(self._h, k, int(width)), "bst_plan_set_gridding")
+        return self
+
     def autotune(self, slices: int = 0, cache: str | None = None) -> int:
         """Pick the faster radix schedule by timing both (bst_plan_autotune).
         With a cache path (default: $BST_AUTOTUNE_CACHE if set) the choice is
@@ -114,7 +131,7 @@ class Plan:
         import json
         import os
         cache = cache or os.environ.get("BST_AUTOTUNE_CACHE")
-        key = f"{torch.cuda.get_device_name()}|N={self.rays}|V={self.V}|pad={self.pad_factor}"
+        key = f"{torch.cuda.get_device_name()}|N={self.rays}|V={self.V}|pad={self.pad_factor}|grid={self.gridding}"
         table = {}
         if cache and os.path.exists(cache):
             try:

@@ -30,6 +30,17 @@ struct bst_plan_s {
     // (angle fraction, radius fraction)
     int* geo_J = nullptr;
     float2* geo_f = nullptr;
+    // P5 gridding kernel (BST_GRID_BILINEAR or BST_GRID_KAISER_BESSEL) and the
+    // KB tables: kernel table, deapodization 1/C per output index, per-strip
+    // CSR lists of sample ids (built by bst_plan_set_gridding)
+    int grid_kind = 0;
+    int kb_w = 0;
+    float* kb_tab = nullptr;
+    float* kb_dk = nullptr;         // [N]
+    int* kb_start = nullptr;        // [kb_nstrips + 1]
+    int* kb_list = nullptr;         // [kb_n]
+    size_t kb_n = 0;
+    int kb_nstrips = 0;
     int chunk_pairs = 1;            // slice pairs per chunk of the forward path
     int maxr = 16;                  // FFT radix schedule of the forward path (16 or 8; autotuned)
     // two plan-owned streams that alternate chunks of the forward path (fork
@@ -120,8 +131,15 @@ bst_status_t bst_launch_brute(bst_plan_s* p, const float* sino, int slices, cons
                               void* ws, size_t ws_bytes, cudaStream_t st);
 bst_status_t bst_build_cells(bst_plan_s* p, cudaStream_t st);
 bst_status_t bst_build_geo_table(bst_plan_s* p);
+// KB gridding + column inverse FFT of np pairs (kb.cu)
+bst_status_t bst_launch_kb_col(bst_plan_s* p, const float2* Z, float2* T, int np, cudaStream_t st);
+void bst_free_kb(bst_plan_s* p);
+double bst_bessel_i0(double x);
 size_t bst_adjoint_ws(const bst_plan_s* p, int slices);
 size_t bst_brute_ws(const bst_plan_s* p, int slices, int filtered);
 
 // mode values shared by the launchers
 enum { BSTK_FILTER = 0, BSTK_BACKPROJECT = 1, BSTK_RAW = 2 };
+// flag or-ed into the ray-stage mode: also multiply by the polar cell area
+// |k| (1/4 at k = 0) for KB gridding
+enum { BSTK_KBW = 8 };

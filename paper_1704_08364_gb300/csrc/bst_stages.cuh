@@ -10,7 +10,8 @@
 //              angular geometry table, inverse FFT along r', the N central rows
 //              written to T.
 //   row_unit   the row half of P6 + P7 + P8 for TPC blocks of four rows: inverse
-//              FFT along c', the N central columns scaled by dt dw^2 = N/(2 M^2),
+//              FFT along c', the N central columns scaled by dt dw^2 = N/(2 M^2)
+//              (and by the deapodization of KB gridding when it is used),
 //              Re to slice a and Im to slice b.
 //
 // Every thread of the block calls the unit (the FFT passes contain barriers).
@@ -51,11 +52,13 @@ struct SpecDst {
     __device__ __forceinline__ void store(int k, float2 v) const {
         if (!live) return;
         const int ak = k <= (M >> 1) ? k : M - k;
+        const int md = mode & 7;
         float w;
-        if (mode == BSTK_RAW) w = 1.f;
+        if (md == BSTK_RAW) w = 1.f;
         else if (ak == (M >> 1)) w = 0.f;
-        else if (mode == BSTK_FILTER) w = g ? __ldg(g + ak) : 1.f;
+        else if (md == BSTK_FILTER) w = g ? __ldg(g + ak) : 1.f;
         else w = ak == 0 ? 0.f : __fdiv_rn(two_alpha, (float)ak);
+        if (mode & BSTK_KBW) w *= ak == 0 ? 0.25f : (float)ak;
         z[k] = make_float2(v.x * w, v.y * w);
     }
 };
@@ -200,13 +203,15 @@ struct VolDst {
     int N, M;
     float scale;
     bool live;
+    const float* dk;    // per-column deapodization of KB gridding, or null
     static constexpr bool kSmem = false;
     __device__ __forceinline__ void store(int p, float2 v) const {
         if (!live) return;
         const int c = signed_freq(p, M) + (N >> 1);
         if (c < 0 || c >= N) return;
-        va[c] = v.x * scale;
-        if (vb) vb[c] = v.y * scale;
+        const float s = dk ? scale * __ldg(dk + c) : scale;
+        va[c] = v.x * s;
+        if (vb) vb[c] = v.y * s;
     }
 };
 
@@ -275,10 +280,12 @@ struct SpecDstShift {
     __device__ __forceinline__ void store(int k, float2 v) const {
         if (!live) return;
         const int ak = k <= (M >> 1) ? k : M - k;
+        const int md = mode & 7;
         float w;
         if (ak == (M >> 1)) w = 0.f;
-        else if (mode == BSTK_FILTER) w = g ? __ldg(g + ak) : 1.f;
+        else if (md == BSTK_FILTER) w = g ? __ldg(g + ak) : 1.f;
         else w = ak == 0 ? 0.f : __fdiv_rn(two_alpha, (float)ak);
+        if (mode & BSTK_KBW) w *= ak == 0 ? 0.25f : (float)ak;
         if (pa.shift != 0.f) {
             // exp(+2 pi i k s / M) with s = s_int + s_frac; the integer part reduced exactly mod M
             const int ks = signed_freq(k, M);
@@ -393,7 +400,7 @@ __device__ __forceinline__ void grid_unit(float2* smem, int q0, int V, int N, co
 template <int M, int TPL, int TPC, int MAXR>
 __device__ __forceinline__ void row_unit(float2* smem, int rb0, int N, const float2* __restrict__ Tp,
                                          float* __restrict__ va, float* __restrict__ vb, float scale,
-                                         const float2* __restrict__ tw) {
+                                         const float2* __restrict__ tw, const float* __restrict__ dk = nullptr) {
     const int tile = threadIdx.x / (4 * TPL);
     const int w = threadIdx.x % (4 * TPL);
     const int line = w & 3, t = w >> 2;
@@ -402,7 +409,8 @@ __device__ __forceinline__ void row_unit(float2* smem, int rb0, int N, const flo
     const bool live = r < N;
     const int rr = live ? r : 0;
     TileSrc src{Tp, M, live ? rb : 0, line, live};
-    VolDst dst{va + (size_t)rr * N, vb ? vb + (size_t)rr * N : nullptr, N, M, scale, live};
+    VolDst dst{va + (size_t)rr * N, vb ? vb + (size_t)rr * N : nullptr, N, M,
+               dk ? scale * __ldg(dk + rr) : scale, live, dk};
     SmemLine sm{smem + (tile * 4 + line) * row_line_stride<M>()};
     fft_line<M, TPL, true, MAXR>(t, src, dst, sm, tw);
 }

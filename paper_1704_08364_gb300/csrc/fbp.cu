@@ -90,13 +90,13 @@ __global__ void __launch_bounds__(TPL * CPC, (TPL * CPC <= 256) ? 1024 / (TPL * 
 template <int M, int TPL, int TPC, int MAXR>
 __global__ void __launch_bounds__(4 * TPL * TPC)
     k_row_ifft(const float2* __restrict__ T, int slices, int pair0, int N, float scale, float* __restrict__ vol,
-               const float2* __restrict__ tw) {
+               const float2* __restrict__ tw, const float* __restrict__ dk) {
     extern __shared__ float2 smem[];
     const int pl = blockIdx.y;
     const int sa = 2 * (pair0 + pl), sb = sa + 1;
     row_unit<M, TPL, TPC, MAXR>(smem, blockIdx.x * TPC, N, T + (size_t)pl * ((N + 3) / 4) * 4 * M,
                                 vol + (size_t)sa * N * N, sb < slices ? vol + (size_t)sb * N * N : nullptr, scale,
-                                tw);
+                                tw, dk);
 }
 
 // ---------------------------------------------------------------------------
@@ -140,6 +140,9 @@ bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int 
     const float scale = (float)((double)N / (2.0 * (double)M * (double)M));
     const float two_alpha = (float)(2 * p->alpha);
     const int row_tiles = (N + 3) / 4;
+    const bool kbg = p->grid_kind == BST_GRID_KAISER_BESSEL;
+    if (kbg && mode != BSTK_RAW) mode |= BSTK_KBW;
+    const float* dk = kbg ? p->kb_dk : nullptr;
     if (nl > 1) {
         if (cudaEventRecord(p->ev_fork, st) != cudaSuccess) return BST_ERR_CUDA;
         for (int l = 0; l < nl; ++l)
@@ -161,11 +164,16 @@ bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int 
             k_ray_fft<M, C::TPL, C::LPC1, MAXR><<<dim3((V + C::LPC1 - 1) / C::LPC1, np), C::TPL * C::LPC1, C::S1, s>>>(
                 sino, slices, p0, N, V, mode, g, two_alpha, Z, p->tw);
         bst_timing_mark(p, s, 0);
-        k_grid_col<M, C::TPL, C::CPC, MAXR><<<dim3((M / 2 + C::CPC - 1) / C::CPC, np), C::TPL * C::CPC, C::S2, s>>>(
-            Z, V, N, p->geo_J, p->geo_f, T, p->tw);
+        if (kbg) {
+            const bst_status_t ks = bst_launch_kb_col(p, Z, T, np, s);
+            if (ks != BST_OK) return ks;
+        } else {
+            k_grid_col<M, C::TPL, C::CPC, MAXR><<<dim3((M / 2 + C::CPC - 1) / C::CPC, np), C::TPL * C::CPC, C::S2, s>>>(
+                Z, V, N, p->geo_J, p->geo_f, T, p->tw);
+        }
         bst_timing_mark(p, s, 1);
         k_row_ifft<M, C::TPL, C::TPC, MAXR><<<dim3((row_tiles + C::TPC - 1) / C::TPC, np), 4 * C::TPL * C::TPC, C::S3, s>>>(
-            T, slices, p0, N, scale, vol, p->tw);
+            T, slices, p0, N, scale, vol, p->tw, dk);
         bst_timing_mark(p, s, 2);
     }
     if (nl > 1) {
@@ -254,17 +262,6 @@ bst_status_t bst_build_geo_table(bst_plan_s* p) {
     return cudaDeviceSynchronize() == cudaSuccess ? BST_OK : BST_ERR_CUDA;
 }
 
-// I0(x) from its power series sum_k ((x/2)^(2k) / (k!)^2), in double
-static double bessel_i0(double x) {
-    double term = 1.0, sum = 1.0;
-    const double q = 0.25 * x * x;
-    for (int k = 1; k < 500 && term > 1e-18 * sum; ++k) {
-        term *= q / ((double)k * (double)k);
-        sum += term;
-    }
-    return sum;
-}
-
 extern "C" bst_status_t bst_fbp_prep(bst_plan_t p, const float* d_sino, int slices, const float* d_dark,
                                      const float* d_flat, float shift, float kb_beta, float kb_halfwidth,
                                      const float* d_g, float* d_volume, void* d_ws, size_t ws_bytes,
@@ -286,6 +283,6 @@ extern "C" bst_status_t bst_fbp_prep(bst_plan_t p, const float* d_sino, int slic
     pa.shift_frac = (float)((double)shift - std::floor((double)shift));
     pa.kb_beta = kb_beta;
     pa.kb_inv_half = kb_beta > 0.f ? 1.f / kb_halfwidth : 0.f;
-    pa.kb_norm = kb_beta > 0.f ? (float)(1.0 / bessel_i0((double)kb_beta)) : 1.f;
+    pa.kb_norm = kb_beta > 0.f ? (float)(1.0 / bst_bessel_i0((double)kb_beta)) : 1.f;
     return bst_launch_forward_prep(p, d_sino, slices, pa, d_g, d_volume, d_ws, ws_bytes, (cudaStream_t)stream);
 }

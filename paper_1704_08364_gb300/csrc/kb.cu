@@ -1,0 +1,229 @@
+// kb.cu -- Kaiser-Bessel gridding for stage P5: plan tables (kernel table,
+// deapodization, per-strip sample lists), the gridding + column-FFT kernel
+// and bst_plan_set_gridding.
+//
+// The paper leaves the interpolation kernel of P5 open.  With KB gridding the
+// path computes, up to the gridding error, the polar quadrature of the inverse
+// 2D Fourier integral x(u) = sum_{j,k} a_jk exp(2 pi i omega_jk . u) with
+// a_jk = dtheta_j dsigma |sigma_k| W[|k|] Y_j[k] (Eq. 3 with the filter of
+// P4), where bilinear interpolation in (kappa, theta) loses several digits.
+// Kernel shape: beta = pi sqrt((W / alpha)^2 (alpha - 1/2)^2 - 0.8) for the
+// grid oversampling alpha = M / N (Beatty, Nishimura and Pauly, 2005).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "bst_kb.cuh"
+
+namespace bst {
+
+template <int M, int MAXR>
+__global__ void __launch_bounds__(tpl_of<M>() * kb_strip_cols<M>(), 1)
+    k_kb_col(const float2* __restrict__ Z, int V, int N, KbArgs kb, float2* __restrict__ T,
+             const float2* __restrict__ tw) {
+    extern __shared__ float2 smem[];
+    const int pl = blockIdx.y;
+    // strips nearest the column c' = 0 carry the most samples: start there
+    const int b = blockIdx.x;
+    const int strip = (b & 1) ? kb.nstrips - 1 - (b >> 1) : (b >> 1);
+    kb_col_unit<M, tpl_of<M>(), MAXR>(smem, strip, V, N, Z + (size_t)pl * V * M, kb,
+                                      T + (size_t)pl * ((N + 3) / 4) * 4 * M, tw);
+}
+
+template <int M, int MAXR>
+bst_status_t launch_kb_col_M(bst_plan_s* p, const float2* Z, float2* T, int np, cudaStream_t st) {
+    constexpr size_t smem = kb_smem_bytes<M>();
+    static const bool attr_ok =
+        cudaFuncSetAttribute(k_kb_col<M, MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
+    if (!attr_ok) return BST_ERR_CUDA;
+    KbArgs a;
+    a.tab = p->kb_tab;
+    a.start = p->kb_start;
+    a.list = p->kb_list;
+    a.dir = p->dir;
+    a.wq = p->wq;
+    a.W = p->kb_w;
+    a.tab_scale = (float)KB_TAB / (float)(p->kb_w / 2);
+    a.nstrips = p->kb_nstrips;
+    k_kb_col<M, MAXR><<<dim3(p->kb_nstrips, np), tpl_of<M>() * kb_strip_cols<M>(), smem, st>>>(Z, p->V, p->N, a, T,
+                                                                                                p->tw);
+    return BST_OK;
+}
+
+template <int M>
+constexpr int kb_cols_host() {
+    return kb_strip_cols<M>();
+}
+
+}  // namespace bst
+
+#define BST_FOR_EACH_M(X) \
+    X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(48) X(96) X(192) X(384) X(768) X(1536) X(3072)
+
+bst_status_t bst_launch_kb_col(bst_plan_s* p, const float2* Z, float2* T, int np, cudaStream_t st) {
+    switch (p->M) {
+#define BST_CASE(m)                                                                            \
+    case m:                                                                                    \
+        return p->maxr == 8 ? bst::launch_kb_col_M<m, 8>(p, Z, T, np, st)                      \
+                            : bst::launch_kb_col_M<m, 16>(p, Z, T, np, st);
+        BST_FOR_EACH_M(BST_CASE)
+#undef BST_CASE
+    }
+    return BST_ERR_UNSUPPORTED_SIZE;
+}
+
+static int kb_strip_cols_of(int M) {
+    switch (M) {
+#define BST_CASE(m) \
+    case m: return bst::kb_cols_host<m>();
+        BST_FOR_EACH_M(BST_CASE)
+#undef BST_CASE
+    }
+    return 0;
+}
+
+double bst_bessel_i0(double x) {
+    double term = 1.0, sum = 1.0;
+    const double q = 0.25 * x * x;
+    for (int k = 1; k < 500 && term > 1e-18 * sum; ++k) {
+        term *= q / ((double)k * (double)k);
+        sum += term;
+    }
+    return sum;
+}
+
+void bst_free_kb(bst_plan_s* p) {
+    cudaFree(p->kb_tab);
+    cudaFree(p->kb_dk);
+    cudaFree(p->kb_start);
+    cudaFree(p->kb_list);
+    p->kb_tab = p->kb_dk = nullptr;
+    p->kb_start = p->kb_list = nullptr;
+    p->kb_w = 0;
+    p->kb_n = 0;
+    p->kb_nstrips = 0;
+}
+
+// Tables of KB gridding of width W for the plan (host-built in double, then
+// uploaded).  Every sample (j, k), k != 0, -M/2, is listed in each strip its
+// footprint touches, widened by one column on each side so that a rounding
+// difference between this double-precision placement and the kernel's float
+// placement can never drop a contribution.
+static bst_status_t build_kb(bst_plan_s* p, int W) {
+    const int M = p->M, V = p->V, N = p->N;
+    const int CS = kb_strip_cols_of(M);
+    if (CS <= 0) return BST_ERR_UNSUPPORTED_SIZE;
+    const int ns = M / CS;
+    const double alpha = (double)M / (double)N;
+    const double beta = M_PI * std::sqrt((W / alpha) * (W / alpha) * (alpha - 0.5) * (alpha - 0.5) - 0.8);
+    const double i0b = bst_bessel_i0(beta);
+
+    // phi(x) = (I0(beta sqrt(1 - (2x/W)^2)) - 1) / (I0(beta) - 1): the KB kernel
+    // without its pedestal, zero at |x| = W/2, so that a footprint edge falling
+    // exactly on a grid point adds nothing and the gridded spectrum of a real
+    // slice stays Hermitian (the pair packing relies on it)
+    std::vector<float> tab(bst::KB_TAB + 2);
+    for (int i = 0; i <= bst::KB_TAB; ++i) {
+        const double u = (double)i / bst::KB_TAB;   // 2x / W
+        tab[i] = (float)((bst_bessel_i0(beta * std::sqrt(std::max(1.0 - u * u, 0.0))) - 1.0) / (i0b - 1.0));
+    }
+    tab[bst::KB_TAB + 1] = tab[bst::KB_TAB];
+
+    // 1 / C(nu), C(nu) = W (sinh(z) / z - sinc(W nu)) / (I0(beta) - 1),
+    // z = sqrt(beta^2 - (pi W nu)^2), sinc(x) = sin(pi x) / (pi x)
+    std::vector<float> dk(N);
+    for (int i = 0; i < N; ++i) {
+        const double nu = (double)(i - N / 2) / (double)M;
+        const double z2 = beta * beta - (M_PI * W * nu) * (M_PI * W * nu);
+        const double z = std::sqrt(std::fabs(z2));
+        const double r = z < 1e-8 ? 1.0 : (z2 >= 0 ? std::sinh(z) / z : std::sin(z) / z);
+        const double a = M_PI * W * nu;
+        const double sn = a == 0.0 ? 1.0 : std::sin(a) / a;
+        dk[i] = (float)((i0b - 1.0) / (W * (r - sn)));
+    }
+
+    std::vector<double> c(V);
+    for (int j = 0; j < V; ++j) c[j] = std::cos(p->theta[j]);
+    auto for_each_strip = [&](int j, int kidx, auto&& fn) {
+        const int k = kidx < M / 2 ? kidx : kidx - M;
+        const double cs = (double)k * c[j];
+        const int f0 = (int)std::floor(cs - 0.5 * W) + 1;
+        int last = -1;
+        for (int f = f0 - 1; f <= f0 + W; ++f) {
+            const int idx = f < 0 ? f + M : (f >= M ? f - M : f);
+            const int s = idx / CS;
+            if (s != last) {
+                fn(s);
+                last = s;
+            }
+        }
+    };
+    std::vector<int> start(ns + 1, 0);
+    for (int j = 0; j < V; ++j)
+        for (int kidx = 1; kidx < M; ++kidx)
+            if (kidx != M / 2) for_each_strip(j, kidx, [&](int s) { ++start[s + 1]; });
+    for (int s = 0; s < ns; ++s) start[s + 1] += start[s];
+    const size_t n = (size_t)start[ns];
+    std::vector<int> list(n);
+    std::vector<int> fill(start.begin(), start.end() - 1);
+    for (int j = 0; j < V; ++j)
+        for (int kidx = 1; kidx < M; ++kidx)
+            if (kidx != M / 2) for_each_strip(j, kidx, [&](int s) { list[fill[s]++] = j * M + kidx; });
+
+    bst_free_kb(p);
+    bool ok = cudaMalloc((void**)&p->kb_tab, tab.size() * sizeof(float)) == cudaSuccess &&
+              cudaMalloc((void**)&p->kb_dk, dk.size() * sizeof(float)) == cudaSuccess &&
+              cudaMalloc((void**)&p->kb_start, start.size() * sizeof(int)) == cudaSuccess &&
+              cudaMalloc((void**)&p->kb_list, std::max<size_t>(n, 1) * sizeof(int)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        bst_free_kb(p);
+        return BST_ERR_OUT_OF_MEMORY;
+    }
+    ok = cudaMemcpy(p->kb_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(p->kb_dk, dk.data(), dk.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
+         cudaMemcpy(p->kb_start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
+         (n == 0 || cudaMemcpy(p->kb_list, list.data(), n * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess);
+    if (!ok) {
+        bst_free_kb(p);
+        return BST_ERR_CUDA;
+    }
+    p->kb_w = W;
+    p->kb_n = n;
+    p->kb_nstrips = ns;
+    return BST_OK;
+}
+
+extern "C" {
+
+bst_status_t bst_plan_set_gridding(bst_plan_t p, int kind, int width) {
+    if (!p) return BST_ERR_INVALID_ARGUMENT;
+    if (kind == BST_GRID_BILINEAR) {
+        cudaDeviceSynchronize();
+        bst_free_kb(p);
+        p->grid_kind = BST_GRID_BILINEAR;
+        return BST_OK;
+    }
+    if (kind != BST_GRID_KAISER_BESSEL || width < 2 || width > bst::KB_WMAX || width % 2 != 0)
+        return BST_ERR_INVALID_ARGUMENT;
+    if (p->grid_kind == BST_GRID_KAISER_BESSEL && p->kb_w == width) return BST_OK;
+    cudaDeviceSynchronize();
+    const bst_status_t s = build_kb(p, width);
+    if (s != BST_OK) {
+        p->grid_kind = BST_GRID_BILINEAR;
+        return s;
+    }
+    p->grid_kind = BST_GRID_KAISER_BESSEL;
+    return BST_OK;
+}
+
+bst_status_t bst_plan_get_gridding(bst_plan_t p, int* kind, int* width) {
+    if (!p || !kind || !width) return BST_ERR_INVALID_ARGUMENT;
+    *kind = p->grid_kind;
+    *width = p->grid_kind == BST_GRID_KAISER_BESSEL ? p->kb_w : 2;
+    return BST_OK;
+}
+
+}  // extern "C"

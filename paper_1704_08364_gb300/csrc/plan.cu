@@ -46,6 +46,7 @@ void free_plan(bst_plan_s* p) {
     cudaFree(p->cell_w);
     cudaFree(p->geo_J);
     cudaFree(p->geo_f);
+    bst_free_kb(p);
     delete p;
 }
 
@@ -285,6 +286,7 @@ bst_status_t radon_adjoint(bst_plan_t p, bst_mode_t mode, const float* d_g, cons
     bst_status_t s = check_io(p, d_sino, slices, d_volume);
     if (s != BST_OK) return s;
     if (mode != BST_W_FILTER && mode != BST_W_BACKPROJECT) return BST_ERR_INVALID_ARGUMENT;
+    if (p->grid_kind != BST_GRID_BILINEAR) return BST_ERR_INVALID_ARGUMENT;
     const size_t need = bst_adjoint_ws(p, slices);
     if (!d_ws || ws_bytes < need) return BST_ERR_WORKSPACE_TOO_SMALL;
     return bst_launch_adjoint(p, mode == BST_W_FILTER ? BSTK_FILTER : BSTK_BACKPROJECT,
@@ -296,7 +298,7 @@ bst_status_t bst_fbp_filter_grad(bst_plan_t p, const float* d_sino, const float*
                                  float* d_grad_g, void* d_ws, size_t ws_bytes, bst_stream_t stream) {
     bst_status_t s = check_io(p, d_sino, slices, d_grad_vol);
     if (s != BST_OK) return s;
-    if (!d_grad_g) return BST_ERR_INVALID_ARGUMENT;
+    if (!d_grad_g || p->grid_kind != BST_GRID_BILINEAR) return BST_ERR_INVALID_ARGUMENT;
     const size_t need = bst_adjoint_ws(p, slices);
     if (!d_ws || ws_bytes < need) return BST_ERR_WORKSPACE_TOO_SMALL;
     return bst_launch_filter_grad(p, d_sino, d_grad_vol, slices, d_grad_g, d_ws, ws_bytes, (cudaStream_t)stream);

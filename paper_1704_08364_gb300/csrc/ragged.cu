@@ -292,6 +292,7 @@ bst_status_t bst_ragged_bind(bst_ragged_t r, const float* const* d_sinos, const 
     for (int k = 0; k < pairs; ++k) {
         const int a = r->first[k], b = r->second[k];
         const bst_plan_s* p = r->plans[a];
+        if (p->grid_kind != BST_GRID_BILINEAR) return BST_ERR_INVALID_ARGUMENT;
         const float* ga = d_g ? d_g[a] : nullptr;
         const float* gb = (d_g && b >= 0) ? d_g[b] : nullptr;
         if (b >= 0 && ga != gb) return BST_ERR_INVALID_ARGUMENT;   // a pair shares its filter

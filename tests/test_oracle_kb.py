@@ -42,6 +42,7 @@ def test_kernel_is_normalised_and_even():
     x = np.linspace(0, 3, 37)
     assert np.array_equal(kb.kb_kernel(x, 6, beta), kb.kb_kernel(-x, 6, beta))
     assert kb.kb_kernel(3.0001, 6, beta) == 0.0
+    assert kb.kb_kernel(3.0, 6, beta) == 0.0    # no pedestal: ties at the support edge carry no weight
 
 
 @pytest.mark.parametrize("mode_g", ["ramp", "taps"])
