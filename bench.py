@@ -238,6 +238,39 @@ def bench_pad1(bst, theta, sino, vol, steps, hbm_peak):
             "path_hbm_frac": alg / (ms / 1e3) / 1e9 / hbm_peak}
 
 
+def stage_avg_us(plan, fn, steps, names=("k_ray_fft", "k_grid_col", "k_row_ifft")):
+    """Average device time per launch of the three forward kernels (the
+    library's per-launch events, single stream)."""
+    import ctypes
+    from paper_1704_08364_gb300 import _lib
+    L = _lib.load()
+    L.bst_plan_set_timing(plan._h, 1)
+    for _ in range(steps):
+        fn()
+    sms = (ctypes.c_double * 8)()
+    sl = (ctypes.c_longlong * 8)()
+    L.bst_plan_timing(plan._h, sms, sl, 8)
+    L.bst_plan_set_timing(plan._h, 0)
+    return {names[i]: 1e3 * sms[i] / max(sl[i], 1) for i in range(3)}
+
+
+def bench_kb(bst, theta, sino, vol, steps):
+    """The same volume with Kaiser-Bessel gridding in P5 (W = 6) at pad factors
+    2 and 1: the spread + column FFT kernel replaces the bilinear gather."""
+    S, V, N = sino.shape
+    out = {}
+    for pad in (2, 1):
+        plan = bst.Plan(N, theta, pad)
+        plan.set_gridding("kaiser-bessel", 6)
+        run = lambda: plan.fbp(sino, out=vol)
+        run()
+        ms = _event_ms(run, steps)
+        out[f"pad{pad}"] = {"M": plan.M, "width": 6, "ms_per_step": ms, "voxels_per_s": S * N * N / (ms / 1e3),
+                            "stage_avg_us": stage_avg_us(plan, run, 2, ("k_ray_fft", "k_kb_col", "k_row_ifft"))}
+        del plan
+    return out
+
+
 def run_reference(args, rank, world):
     N = V = args.rays
     if rank != 0:
@@ -386,9 +419,10 @@ def run_ours(args, rank, world):
 
     # the ragged batch: 64 sinograms of mixed sizes, one persistent launch
     # (direct and replayed from a CUDA graph) vs plain per-size launches
-    ragged = autograd = pad1 = None
+    ragged = autograd = pad1 = kbg = None
     if not args.no_extras:
         pad1 = bench_pad1(bst, theta, sino, vol, args.steps, hbm_peak)
+        kbg = bench_kb(bst, theta, sino, vol, args.steps)
         ragged = bench_ragged(bst, synth, sdev, dev, args.steps)
         autograd = bench_autograd(bst, synth, dev, args.steps)
 
@@ -412,7 +446,7 @@ def run_ours(args, rank, world):
             "vs_brute": {"brute_ms_per_slice": brute_ms_per_slice, "bst_ms_per_slice": bst_ms_per_slice,
                          "speedup": brute_ms_per_slice / bst_ms_per_slice, "brute_slices_timed": bs},
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": 3 * ((S + 1) // 2) * args.steps,
-            "pad1": pad1, "ragged": ragged, "autograd": autograd,
+            "pad1": pad1, "kb_gridding": kbg, "ragged": ragged, "autograd": autograd,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

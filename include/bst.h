@@ -232,10 +232,10 @@ int bst_plan_get_schedule(bst_plan_t plan);
  *     alpha = 2), which bilinear interpolation reaches only to ~1e-1.  At
  *     alpha = 1 the grid has no guard band: accurate inside the inscribed
  *     disk, ill-conditioned (deapodization gain up to ~1e7) at the edge.
- * Builds the plan's KB tables (a kernel table, the deapodization and, per
- * strip of Cartesian columns, the list of samples whose footprint touches
- * it: about 4 (1 + (W + 2) / CS) V M bytes) synchronously; synchronises the
- * device.  radon_adjoint, bst_fbp_filter_grad and the ragged batch need a
+ * Builds the plan's KB tables synchronously (a kernel table, the
+ * deapodization and, per strip of four Cartesian columns, the samples whose
+ * footprint meets it with their work items: about 4 (1 + (W - 1) / 4) V M
+ * bytes, ~90 MB at N = V = 2048, alpha = 2, W = 6); synchronises the device.  radon_adjoint, bst_fbp_filter_grad and the ragged batch need a
  * bilinear plan and reject a KB one.  Errors: INVALID_ARGUMENT (kind, width),
  * OUT_OF_MEMORY, CUDA (the plan then stays bilinear). */
 bst_status_t bst_plan_set_gridding(bst_plan_t plan, int kind, int width);

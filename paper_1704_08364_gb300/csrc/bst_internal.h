@@ -32,13 +32,14 @@ struct bst_plan_s {
     float2* geo_f = nullptr;
     // P5 gridding kernel (BST_GRID_BILINEAR or BST_GRID_KAISER_BESSEL) and the
     // KB tables: kernel table, deapodization 1/C per output index, per-strip
-    // CSR lists of sample ids (built by bst_plan_set_gridding)
+    // sample lists and work items (built by bst_plan_set_gridding)
     int grid_kind = 0;
     int kb_w = 0;
     float* kb_tab = nullptr;
     float* kb_dk = nullptr;         // [N]
-    int* kb_start = nullptr;        // [kb_nstrips + 1]
-    int* kb_list = nullptr;         // [kb_n]
+    int* kb_start = nullptr;        // [kb_nstrips + 1] first work item of each strip
+    int* kb_list = nullptr;         // [kb_n] sample ids
+    int4* kb_items = nullptr;       // (band, first entry, end entry, 0)
     size_t kb_n = 0;
     int kb_nstrips = 0;
     int chunk_pairs = 1;            // slice pairs per chunk of the forward path

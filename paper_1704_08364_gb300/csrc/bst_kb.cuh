@@ -10,18 +10,28 @@
 // without its pedestal, zero at the support edge), on the M-periodic grid.
 // The division by phi's transform (deapodization) happens in the row stage.
 //
-// One block owns a strip of CS consecutive Cartesian columns (storage order),
-// kept in shared memory as CS padded FFT lines: it zeroes them, spreads the
-// strip's samples (the plan lists, per strip, every sample whose footprint
-// touches it) with shared-memory atomics, then runs the inverse FFT along r'
-// of each column in place and writes the N central rows to T exactly as the
-// bilinear gather does.  The V samples of the DC bin all sit at the origin;
-// one warp sums them (with their angular weights) and spreads the sum once.
+// One block owns a strip of four consecutive Cartesian columns (storage
+// order), kept in shared memory as four padded FFT lines.  The plan lists, per
+// strip, every sample whose footprint touches it, sorted by the first row of
+// the footprint, and cuts the strip into bands of four rows: a band's samples
+// are then one contiguous range of that list (two at the periodic wrap), which
+// the plan splits into work items of at most KB_ITEM entries.  A thread takes
+// an item, accumulates the 4 x 4 cell of its band in registers (the weight of
+// every sample at every cell point, zero outside the footprint) and adds the
+// cell to shared memory once, so heavy bands near the origin are shared by
+// many threads and the atomics are one per cell point and item, not per
+// sample.  Then the inverse FFT along r' of each column runs in place and the
+// N central rows go to T exactly as with the bilinear gather.  The V samples
+// of the DC bin all sit at the origin; one warp sums them (with their angular
+// weights) and spreads the sum once.
 //
 // Positions are exact to float rounding of a number below one: k cos(theta)
 // is split into the nearest integer and a remainder with the double-float
 // direction table and FMA, so the kernel weights do not lose the ~1e-4 bin
-// that a plain float product loses at radius 2048.
+// that a plain float product loses at radius 2048.  Weights come from the
+// exact distance to each cell point, so which samples the plan lists (in
+// double precision) only has to be a superset of the float footprints up to
+// the kernel's zero edge.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -31,10 +41,14 @@ namespace bst {
 
 constexpr int KB_TAB = 8192;   // table intervals over [0, W/2]
 constexpr int KB_WMAX = 8;
+constexpr int KB_CS = 4;       // columns per strip
+constexpr int KB_RB = 4;       // rows per band
+constexpr int KB_ITEM = 64;    // entries per work item at most (16 and 128 measured slower)
 
 struct KbArgs {
-    const float* tab;      // [KB_TAB + 2] phi(i W / (2 KB_TAB)); the last entry repeats
-    const int* start;      // [nstrips + 1] CSR offsets of the strips' sample lists
+    const float* tab;      // [KB_TAB + 2] phi(i W / (2 KB_TAB)); zero from i = KB_TAB on
+    const int* istart;     // [nstrips + 1] offsets of the strips' work items
+    const int4* items;     // (band, first entry, end entry, 0)
     const int* list;       // sample ids j M + kidx (natural-order bin index)
     const float4* dir;     // [V + 2] (cos_hi, cos_lo, sin_hi, sin_lo) of theta_{j}, at j + 1
     const float* wq;       // [V] angular weights dtheta_j
@@ -43,19 +57,18 @@ struct KbArgs {
     int nstrips;
 };
 
-// columns per strip: CS lines of TPL threads fill a 1024-thread block
-template <int M> __host__ __device__ constexpr int kb_strip_cols() {
-    return (1024 / tpl_of<M>()) < M ? 1024 / tpl_of<M>() : M;
-}
+template <int M> __host__ __device__ constexpr int kb_threads() { return KB_CS * tpl_of<M>(); }
 
 template <int M> __host__ __device__ constexpr size_t kb_smem_bytes() {
-    return (size_t)kb_strip_cols<M>() * smem_line_len(M) * sizeof(float2) + (size_t)(KB_TAB + 2) * sizeof(float);
+    return (size_t)KB_CS * smem_line_len(M) * sizeof(float2) + (size_t)(KB_TAB + 2) * sizeof(float);
 }
 
+// phi(|x|) by linear interpolation in the table; zero for |x| >= W/2 (the
+// index saturates on the zero entries; branch-free measured faster than
+// skipping the lookup)
 __device__ __forceinline__ float kb_phi(const float* tab, float x, float scale) {
     const float u = fabsf(x) * scale;
-    int i = (int)u;
-    i = i < KB_TAB ? i : KB_TAB;
+    const int i = (int)fminf(u, (float)KB_TAB);
     const float f = u - (float)i;
     const float a = tab[i];
     return fmaf(f, tab[i + 1] - a, a);
@@ -69,64 +82,26 @@ __device__ __forceinline__ void kb_split(float k, float hi, float lo, float& n, 
     d = __fadd_rn(__fsub_rn(p, n), e);
 }
 
-// Spread one sample of value z at (nc + dc, nr + dr) bins into the strip's
-// columns [c0, c0 + CS).  Strip-local lines of length LL (padded index).
-template <int M, int CS>
-__device__ __forceinline__ void kb_spread(float2* smem, const float* tab, const KbArgs& kb, int c0, float nc,
-                                          float dc, float nr, float dr, float2 z) {
-    constexpr int LL = smem_line_len(M);
-    const int hw = kb.W >> 1;
-    const int fc0 = (int)nc - hw + (dc < 0.f ? 0 : 1);
-    const int fr0 = (int)nr - hw + (dr < 0.f ? 0 : 1);
-    const float xc0 = (float)(fc0 - (int)nc) - dc;
-    const float xr0 = (float)(fr0 - (int)nr) - dr;
-    float wr[KB_WMAX];
-#pragma unroll
-    for (int i = 0; i < KB_WMAX; ++i) wr[i] = i < kb.W ? kb_phi(tab, xr0 + (float)i, kb.tab_scale) : 0.f;
-#pragma unroll
-    for (int ic = 0; ic < KB_WMAX; ++ic) {
-        if (ic >= kb.W) break;
-        const int fc = fc0 + ic;
-        const int lc = (fc < 0 ? fc + M : fc) - c0;
-        if ((unsigned)lc >= (unsigned)CS) continue;
-        const float wc = kb_phi(tab, xc0 + (float)ic, kb.tab_scale);
-        const float2 zc = make_float2(wc * z.x, wc * z.y);
-        float* line = reinterpret_cast<float*>(smem + lc * LL);
-#pragma unroll
-        for (int ir = 0; ir < KB_WMAX; ++ir) {
-            if (ir >= kb.W) break;
-            const int fr = fr0 + ir;
-            const int rr = fr < 0 ? fr + M : fr;
-            const int o = 2 * (rr + (rr >> 4));
-            atomicAdd(line + o, wr[ir] * zc.x);
-            atomicAdd(line + o + 1, wr[ir] * zc.y);
-        }
-    }
+// signed distance (in bins, periodic in M) from the sample at n + d to grid index g
+template <int M>
+__device__ __forceinline__ float kb_dist(int g, float n, float d) {
+    int q = g - (int)n;
+    q = q >= (M >> 1) ? q - M : (q < -(M >> 1) ? q + M : q);
+    return (float)q - d;
 }
 
-// P5 (KB gridding) + column P6 for the strip of CS columns starting at c0 of
-// one slice pair (blockDim = TPL * CS).
-template <int M, int TPL, int MAXR>
-__device__ __forceinline__ void kb_col_unit(float2* smem, int strip, int V, int N, const float2* __restrict__ Zp,
-                                            const KbArgs& kb, float2* __restrict__ Tp,
-                                            const float2* __restrict__ tw) {
-    constexpr int CS = kb_strip_cols<M>();
-    constexpr int NT = TPL * CS;
+// accumulate the samples of entries [lo, hi) into the 4 x 4 cell (rows r0..r0+3,
+// columns c0..c0+3) and add the cell to the strip's shared-memory lines
+template <int M>
+__device__ __forceinline__ void kb_item(float2* smem, const float* tab, const KbArgs& kb, const float2* __restrict__ Zp,
+                                        int c0, int r0, int lo, int hi) {
     constexpr int LL = smem_line_len(M);
-    float* tab = reinterpret_cast<float*>(smem + CS * LL);
-    const int tid = threadIdx.x;
-    for (int i = tid; i < KB_TAB + 2; i += NT) tab[i] = __ldg(kb.tab + i);
-    for (int i = tid; i < CS * LL; i += NT) smem[i] = make_float2(0.f, 0.f);
-    __syncthreads();
-    const int c0 = strip * CS;
-
-    // the strip's samples; lanes of a warp take entries NT / 32 apart so that
-    // their footprints (neighbouring samples of one ray overlap) rarely collide
-    const int e0 = __ldg(kb.start + strip), e1 = __ldg(kb.start + strip + 1);
-    const int slot = (NT % 32 == 0) ? (tid & 31) * (NT / 32) + (tid >> 5) : tid;
-    for (int base = e0; base < e1; base += NT) {
-        const int e = base + slot;
-        if (e >= e1) continue;
+    float ax[KB_CS][KB_RB], ay[KB_CS][KB_RB];
+#pragma unroll
+    for (int c = 0; c < KB_CS; ++c)
+#pragma unroll
+        for (int r = 0; r < KB_RB; ++r) ax[c][r] = ay[c][r] = 0.f;
+    for (int e = lo; e < hi; ++e) {
         const int s = __ldg(kb.list + e);
         const int j = s / M;
         const int kidx = s - j * M;
@@ -137,45 +112,102 @@ __device__ __forceinline__ void kb_col_unit(float2* smem, int strip, int V, int 
         kb_split(k, d.z, d.w, nr, dr);
         const float2 zz = __ldg(Zp + s);
         const float wa = __ldg(kb.wq + j);
-        kb_spread<M, CS>(smem, tab, kb, c0, nc, dc, nr, dr, make_float2(wa * zz.x, wa * zz.y));
+        float wr[KB_RB];
+#pragma unroll
+        for (int r = 0; r < KB_RB; ++r) wr[r] = kb_phi(tab, kb_dist<M>(r0 + r, nr, dr), kb.tab_scale);
+#pragma unroll
+        for (int c = 0; c < KB_CS; ++c) {
+            const float wc = wa * kb_phi(tab, kb_dist<M>(c0 + c, nc, dc), kb.tab_scale);
+            const float zx = wc * zz.x, zy = wc * zz.y;
+#pragma unroll
+            for (int r = 0; r < KB_RB; ++r) {
+                ax[c][r] = fmaf(wr[r], zx, ax[c][r]);
+                ay[c][r] = fmaf(wr[r], zy, ay[c][r]);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < KB_CS; ++c) {
+        float* line = reinterpret_cast<float*>(smem + c * LL);
+#pragma unroll
+        for (int r = 0; r < KB_RB; ++r) {
+            const int rr = r0 + r;
+            const int o = 2 * (rr + (rr >> 4));
+            atomicAdd(line + o, ax[c][r]);
+            atomicAdd(line + o + 1, ay[c][r]);
+        }
+    }
+}
+
+// the DC sample at the origin (value z) into the strip's columns
+template <int M>
+__device__ __forceinline__ void kb_spread_dc(float2* smem, const float* tab, const KbArgs& kb, int c0, float2 z) {
+    constexpr int LL = smem_line_len(M);
+    const int hw = kb.W >> 1;
+    for (int c = 0; c < KB_CS; ++c) {
+        const float x = kb_dist<M>(c0 + c, 0.f, 0.f);
+        if (fabsf(x) >= (float)hw) continue;
+        const float wc = kb_phi(tab, x, kb.tab_scale);
+        float* line = reinterpret_cast<float*>(smem + c * LL);
+        for (int r = -hw + 1; r < hw; ++r) {
+            const int rr = r < 0 ? r + M : r;
+            const float w = wc * kb_phi(tab, (float)r, kb.tab_scale);
+            const int o = 2 * (rr + (rr >> 4));
+            atomicAdd(line + o, w * z.x);
+            atomicAdd(line + o + 1, w * z.y);
+        }
+    }
+}
+
+// P5 (KB gridding) + column P6 for the strip of four columns starting at
+// c0 = 4 strip of one slice pair (blockDim = 4 TPL)
+template <int M, int TPL, int MAXR>
+__device__ __forceinline__ void kb_col_unit(float2* smem, int strip, int V, int N, const float2* __restrict__ Zp,
+                                            const KbArgs& kb, float2* __restrict__ Tp,
+                                            const float2* __restrict__ tw) {
+    constexpr int NT = KB_CS * TPL;
+    constexpr int LL = smem_line_len(M);
+    float* tab = reinterpret_cast<float*>(smem + KB_CS * LL);
+    const int tid = threadIdx.x;
+    for (int i = tid; i < KB_TAB + 2; i += NT) tab[i] = __ldg(kb.tab + i);
+    for (int i = tid; i < KB_CS * LL; i += NT) smem[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    const int c0 = strip * KB_CS;
+
+    const int i0 = __ldg(kb.istart + strip), i1 = __ldg(kb.istart + strip + 1);
+    for (int i = i0 + tid; i < i1; i += NT) {
+        const int4 it = __ldg(kb.items + i);
+        kb_item<M>(smem, tab, kb, Zp, c0, KB_RB * it.x, it.y, it.z);
     }
 
     // the DC bin of every angle sits at the origin: one weighted sum, spread once
-    {
-        const int hw = kb.W >> 1;
-        bool here = false;
-        for (int ic = 0; ic < kb.W; ++ic) {
-            const int fc = ic - hw + 1;
-            here |= (unsigned)((fc < 0 ? fc + M : fc) - c0) < (unsigned)CS;
-        }
-        if (here) {
-            if constexpr (NT >= 32) {
-                if (tid < 32) {
-                    float sx = 0.f, sy = 0.f;
-                    for (int j = tid; j < V; j += 32) {
-                        const float w = __ldg(kb.wq + j);
-                        const float2 zz = __ldg(Zp + (size_t)j * M);
-                        sx = fmaf(w, zz.x, sx);
-                        sy = fmaf(w, zz.y, sy);
-                    }
+    if (c0 < (kb.W >> 1) || c0 + KB_CS > M - (kb.W >> 1)) {
+        if constexpr (NT >= 32) {
+            if (tid < 32) {
+                float sx = 0.f, sy = 0.f;
+                for (int j = tid; j < V; j += 32) {
+                    const float w = __ldg(kb.wq + j);
+                    const float2 zz = __ldg(Zp + (size_t)j * M);
+                    sx = fmaf(w, zz.x, sx);
+                    sy = fmaf(w, zz.y, sy);
+                }
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        sx += __shfl_xor_sync(0xffffffffu, sx, o);
-                        sy += __shfl_xor_sync(0xffffffffu, sy, o);
-                    }
-                    if (tid == 0) kb_spread<M, CS>(smem, tab, kb, c0, 0.f, 0.f, 0.f, 0.f, make_float2(sx, sy));
+                for (int o = 16; o > 0; o >>= 1) {
+                    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                    sy += __shfl_xor_sync(0xffffffffu, sy, o);
                 }
-            } else {
-                if (tid == 0) {
-                    float sx = 0.f, sy = 0.f;
-                    for (int j = 0; j < V; ++j) {
-                        const float w = __ldg(kb.wq + j);
-                        const float2 zz = __ldg(Zp + (size_t)j * M);
-                        sx = fmaf(w, zz.x, sx);
-                        sy = fmaf(w, zz.y, sy);
-                    }
-                    kb_spread<M, CS>(smem, tab, kb, c0, 0.f, 0.f, 0.f, 0.f, make_float2(sx, sy));
+                if (tid == 0) kb_spread_dc<M>(smem, tab, kb, c0, make_float2(sx, sy));
+            }
+        } else {
+            if (tid == 0) {
+                float sx = 0.f, sy = 0.f;
+                for (int j = 0; j < V; ++j) {
+                    const float w = __ldg(kb.wq + j);
+                    const float2 zz = __ldg(Zp + (size_t)j * M);
+                    sx = fmaf(w, zz.x, sx);
+                    sy = fmaf(w, zz.y, sy);
                 }
+                kb_spread_dc<M>(smem, tab, kb, c0, make_float2(sx, sy));
             }
         }
     }

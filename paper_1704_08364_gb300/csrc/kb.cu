@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <vector>
 
 #include "bst_kb.cuh"
@@ -20,7 +21,7 @@
 namespace bst {
 
 template <int M, int MAXR>
-__global__ void __launch_bounds__(tpl_of<M>() * kb_strip_cols<M>(), 1)
+__global__ void __launch_bounds__(kb_threads<M>(), 1)
     k_kb_col(const float2* __restrict__ Z, int V, int N, KbArgs kb, float2* __restrict__ T,
              const float2* __restrict__ tw) {
     extern __shared__ float2 smem[];
@@ -40,21 +41,16 @@ bst_status_t launch_kb_col_M(bst_plan_s* p, const float2* Z, float2* T, int np, 
     if (!attr_ok) return BST_ERR_CUDA;
     KbArgs a;
     a.tab = p->kb_tab;
-    a.start = p->kb_start;
+    a.istart = p->kb_start;
+    a.items = p->kb_items;
     a.list = p->kb_list;
     a.dir = p->dir;
     a.wq = p->wq;
     a.W = p->kb_w;
     a.tab_scale = (float)KB_TAB / (float)(p->kb_w / 2);
     a.nstrips = p->kb_nstrips;
-    k_kb_col<M, MAXR><<<dim3(p->kb_nstrips, np), tpl_of<M>() * kb_strip_cols<M>(), smem, st>>>(Z, p->V, p->N, a, T,
-                                                                                                p->tw);
+    k_kb_col<M, MAXR><<<dim3(p->kb_nstrips, np), kb_threads<M>(), smem, st>>>(Z, p->V, p->N, a, T, p->tw);
     return BST_OK;
-}
-
-template <int M>
-constexpr int kb_cols_host() {
-    return kb_strip_cols<M>();
 }
 
 }  // namespace bst
@@ -74,16 +70,6 @@ bst_status_t bst_launch_kb_col(bst_plan_s* p, const float2* Z, float2* T, int np
     return BST_ERR_UNSUPPORTED_SIZE;
 }
 
-static int kb_strip_cols_of(int M) {
-    switch (M) {
-#define BST_CASE(m) \
-    case m: return bst::kb_cols_host<m>();
-        BST_FOR_EACH_M(BST_CASE)
-#undef BST_CASE
-    }
-    return 0;
-}
-
 double bst_bessel_i0(double x) {
     double term = 1.0, sum = 1.0;
     const double q = 0.25 * x * x;
@@ -99,23 +85,35 @@ void bst_free_kb(bst_plan_s* p) {
     cudaFree(p->kb_dk);
     cudaFree(p->kb_start);
     cudaFree(p->kb_list);
+    cudaFree(p->kb_items);
     p->kb_tab = p->kb_dk = nullptr;
     p->kb_start = p->kb_list = nullptr;
+    p->kb_items = nullptr;
     p->kb_w = 0;
     p->kb_n = 0;
     p->kb_nstrips = 0;
 }
 
-// Tables of KB gridding of width W for the plan (host-built in double, then
-// uploaded).  Every sample (j, k), k != 0, -M/2, is listed in each strip its
-// footprint touches, widened by one column on each side so that a rounding
-// difference between this double-precision placement and the kernel's float
-// placement can never drop a contribution.
+template <class T>
+static bool upload_vec(T** d, const std::vector<T>& h) {
+    if (cudaMalloc((void**)d, std::max<size_t>(h.size(), 1) * sizeof(T)) != cudaSuccess) return false;
+    return h.empty() || cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
+// Tables of KB gridding of width W for the plan, host-built in double:
+//   the kernel table and the deapodization;
+//   per strip of four columns, every sample (j, k), k != 0, -M/2, whose
+//   footprint (the W columns c' - c_s in (-W/2, W/2]) meets the strip, sorted
+//   by the first row of its footprint (r' - r_s > -W/2, taken mod M);
+//   per band of four rows of the strip, the range of that list whose footprint
+//   meets the band (two ranges at the wrap), cut into work items of at most
+//   KB_ITEM entries.
 static bst_status_t build_kb(bst_plan_s* p, int W) {
+    using bst::KB_CS;
+    using bst::KB_ITEM;
+    using bst::KB_RB;
     const int M = p->M, V = p->V, N = p->N;
-    const int CS = kb_strip_cols_of(M);
-    if (CS <= 0) return BST_ERR_UNSUPPORTED_SIZE;
-    const int ns = M / CS;
+    const int ns = M / KB_CS, nb = M / KB_RB;
     const double alpha = (double)M / (double)N;
     const double beta = M_PI * std::sqrt((W / alpha) * (W / alpha) * (alpha - 0.5) * (alpha - 0.5) - 0.8);
     const double i0b = bst_bessel_i0(beta);
@@ -129,7 +127,8 @@ static bst_status_t build_kb(bst_plan_s* p, int W) {
         const double u = (double)i / bst::KB_TAB;   // 2x / W
         tab[i] = (float)((bst_bessel_i0(beta * std::sqrt(std::max(1.0 - u * u, 0.0))) - 1.0) / (i0b - 1.0));
     }
-    tab[bst::KB_TAB + 1] = tab[bst::KB_TAB];
+    tab[bst::KB_TAB] = 0.f;
+    tab[bst::KB_TAB + 1] = 0.f;
 
     // 1 / C(nu), C(nu) = W (sinh(z) / z - sinc(W nu)) / (I0(beta) - 1),
     // z = sqrt(beta^2 - (pi W nu)^2), sinc(x) = sin(pi x) / (pi x)
@@ -144,51 +143,79 @@ static bst_status_t build_kb(bst_plan_s* p, int W) {
         dk[i] = (float)((i0b - 1.0) / (W * (r - sn)));
     }
 
-    std::vector<double> c(V);
-    for (int j = 0; j < V; ++j) c[j] = std::cos(p->theta[j]);
-    auto for_each_strip = [&](int j, int kidx, auto&& fn) {
-        const int k = kidx < M / 2 ? kidx : kidx - M;
-        const double cs = (double)k * c[j];
-        const int f0 = (int)std::floor(cs - 0.5 * W) + 1;
+    // footprint starts (first column and first row, mod M) of every sample
+    std::vector<double> cth(V), sth(V);
+    for (int j = 0; j < V; ++j) {
+        cth[j] = std::cos(p->theta[j]);
+        sth[j] = std::sin(p->theta[j]);
+    }
+    auto first = [&](double x) {
+        const int f = (int)std::floor(x - 0.5 * W) + 1;
+        return f < 0 ? f + M : (f >= M ? f - M : f);
+    };
+    // pass 1: entries per (strip, first row)
+    std::vector<int> cnt((size_t)ns * M + 1, 0);
+    auto strips_of = [&](int fc, auto&& fn) {
         int last = -1;
-        for (int f = f0 - 1; f <= f0 + W; ++f) {
-            const int idx = f < 0 ? f + M : (f >= M ? f - M : f);
-            const int s = idx / CS;
+        for (int d = 0; d < W; ++d) {
+            int c = fc + d;
+            if (c >= M) c -= M;
+            const int s = c / KB_CS;
             if (s != last) {
                 fn(s);
                 last = s;
             }
         }
     };
-    std::vector<int> start(ns + 1, 0);
     for (int j = 0; j < V; ++j)
-        for (int kidx = 1; kidx < M; ++kidx)
-            if (kidx != M / 2) for_each_strip(j, kidx, [&](int s) { ++start[s + 1]; });
-    for (int s = 0; s < ns; ++s) start[s + 1] += start[s];
-    const size_t n = (size_t)start[ns];
+        for (int kidx = 1; kidx < M; ++kidx) {
+            if (kidx == M / 2) continue;
+            const double k = (double)(kidx < M / 2 ? kidx : kidx - M);
+            const int fc = first(k * cth[j]), fr = first(k * sth[j]);
+            strips_of(fc, [&](int s) { ++cnt[(size_t)s * M + fr + 1]; });
+        }
+    for (size_t i = 0; i < (size_t)ns * M; ++i) cnt[i + 1] += cnt[i];
+    const size_t n = (size_t)cnt[(size_t)ns * M];
+    if (n >= (size_t)INT32_MAX) return BST_ERR_UNSUPPORTED_SIZE;
+    // pass 2: the lists, sorted by (strip, first row)
     std::vector<int> list(n);
-    std::vector<int> fill(start.begin(), start.end() - 1);
-    for (int j = 0; j < V; ++j)
-        for (int kidx = 1; kidx < M; ++kidx)
-            if (kidx != M / 2) for_each_strip(j, kidx, [&](int s) { list[fill[s]++] = j * M + kidx; });
+    {
+        std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+        for (int j = 0; j < V; ++j)
+            for (int kidx = 1; kidx < M; ++kidx) {
+                if (kidx == M / 2) continue;
+                const double k = (double)(kidx < M / 2 ? kidx : kidx - M);
+                const int fc = first(k * cth[j]), fr = first(k * sth[j]);
+                strips_of(fc, [&](int s) { list[fill[(size_t)s * M + fr]++] = j * M + kidx; });
+            }
+    }
+    // work items: band b of strip s needs first rows in [KB_RB b - W + 1, KB_RB b + KB_RB - 1] (mod M)
+    std::vector<int4> items;
+    std::vector<int> istart(ns + 1, 0);
+    auto row_pos = [&](int s, int r) { return cnt[(size_t)s * M + r]; };   // first entry with first row >= r
+    auto emit = [&](int b, int lo, int hi) {
+        for (int e = lo; e < hi; e += KB_ITEM) items.push_back(make_int4(b, e, std::min(hi, e + KB_ITEM), 0));
+    };
+    for (int s = 0; s < ns; ++s) {
+        for (int b = 0; b < nb; ++b) {
+            const int lo = KB_RB * b - W + 1, hi = KB_RB * b + KB_RB;   // rows [lo, hi)
+            if (lo >= 0) {
+                emit(b, row_pos(s, lo), row_pos(s, hi));
+            } else {
+                emit(b, row_pos(s, lo + M), row_pos(s, M));
+                emit(b, row_pos(s, 0), row_pos(s, hi));
+            }
+        }
+        istart[s + 1] = (int)items.size();
+    }
 
     bst_free_kb(p);
-    bool ok = cudaMalloc((void**)&p->kb_tab, tab.size() * sizeof(float)) == cudaSuccess &&
-              cudaMalloc((void**)&p->kb_dk, dk.size() * sizeof(float)) == cudaSuccess &&
-              cudaMalloc((void**)&p->kb_start, start.size() * sizeof(int)) == cudaSuccess &&
-              cudaMalloc((void**)&p->kb_list, std::max<size_t>(n, 1) * sizeof(int)) == cudaSuccess;
+    bool ok = upload_vec(&p->kb_tab, tab) && upload_vec(&p->kb_dk, dk) && upload_vec(&p->kb_start, istart) &&
+              upload_vec(&p->kb_list, list) && upload_vec(&p->kb_items, items);
     if (!ok) {
         cudaGetLastError();
         bst_free_kb(p);
         return BST_ERR_OUT_OF_MEMORY;
-    }
-    ok = cudaMemcpy(p->kb_tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(p->kb_dk, dk.data(), dk.size() * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
-         cudaMemcpy(p->kb_start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
-         (n == 0 || cudaMemcpy(p->kb_list, list.data(), n * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess);
-    if (!ok) {
-        bst_free_kb(p);
-        return BST_ERR_CUDA;
     }
     p->kb_w = W;
     p->kb_n = n;
