@@ -58,14 +58,18 @@ def disk_points(M: int) -> int:
     return int(np.count_nonzero(k[None, :] ** 2 + k[:, None] ** 2 < (M // 2) ** 2))
 
 
-def stage_flops(N: int, V: int, M: int) -> dict:
+def stage_flops(N: int, V: int, M: int, kb_width: int = 0) -> dict:
     """Algorithmic flops per launch (one slice pair) of each kernel of the
     forward path: conventional 5 M log2 M per complex FFT line, 6 flops per
     weighted spectrum sample, 12 per bilinear gather (three complex lerps),
-    2 per kept output sample."""
+    2 per kept output sample.  With Kaiser-Bessel gridding of width W the
+    gridding stage counts 6 flops per (sample, grid point) pair of the W x W
+    footprints (a real weight product and a complex multiply-add) for the
+    V (M - 1) polar samples."""
+    grid = 12.0 * disk_points(M) if kb_width <= 0 else 6.0 * kb_width * kb_width * V * (M - 1)
     return {
         0: V * (fft_flops(M) + 6.0 * M),
-        1: M * fft_flops(M) + 12.0 * disk_points(M),
+        1: M * fft_flops(M) + grid,
         2: N * fft_flops(M) + 2.0 * N * N * 2,
     }
 
@@ -309,6 +313,9 @@ def run_ours(args, rank, world):
     alpha = args.pad
     theta = synth.uniform_angles(V)
     plan = bst.Plan(N, theta, alpha)
+    kbw = args.kb_width if args.gridding == "kb" else 0
+    if kbw:
+        plan.set_gridding("kaiser-bessel", kbw)
     M = plan.M
     sino = sdev.ellipse_volume(synth.WORKLOADS["volume-2048"].index, S, V, N, noise_frac=0.01, device=dev)
     vol = torch.empty((S, N, N), dtype=torch.float32, device=dev)
@@ -386,20 +393,23 @@ def run_ours(args, rank, world):
     L.bst_plan_set_timing(plan.handle, 0)
     stage_ms = {s: sms[s] for s in range(3)}
     stage_n = {s: sl[s] for s in range(3)}
-    flops = stage_flops(N, V, M)
+    flops = stage_flops(N, V, M, kbw)
+    names = dict(STAGE_NAMES)
+    if kbw:
+        names[1] = "k_kb_col"
     dom = max(stage_ms, key=lambda s: stage_ms[s])
     avg_ms = stage_ms[dom] / max(stage_n[dom], 1)
     hbm_peak, sm_max, src = _peaks()
     peak_tf = fp32_peak_tflops(sm_max)
     achieved_tf = flops[dom] / (avg_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": STAGE_NAMES[dom], "achieved": achieved_tf, "peak": peak_tf,
+    roofline = {"bound": "alu", "kernel": names[dom], "achieved": achieved_tf, "peak": peak_tf,
                 "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
-                "traffic": captured_traffic(STAGE_NAMES[dom], N, alpha),
+                "traffic": None if kbw else captured_traffic(names[dom], N, alpha),
                 "traffic_note": "DRAM bytes per launch from one cold-cache ncu capture (null if the kernel changed)",
                 "algorithmic_flops_per_launch": flops[dom],
                 "peak_source": "FP32 152 SM x 128 lanes x 2 x %.0f MHz (derived)" % sm_max,
-                "stage_share": {STAGE_NAMES[s]: stage_ms[s] / max(sum(stage_ms.values()), 1e-9) for s in stage_ms},
-                "stage_avg_us": {STAGE_NAMES[s]: 1e3 * stage_ms[s] / max(stage_n[s], 1) for s in stage_ms}}
+                "stage_share": {names[s]: stage_ms[s] / max(sum(stage_ms.values()), 1e-9) for s in stage_ms},
+                "stage_avg_us": {names[s]: 1e3 * stage_ms[s] / max(stage_n[s], 1) for s in stage_ms}}
     alg_bytes = 4.0 * (V * N + N * N) * S
     path_hbm = {"algorithmic_bytes_per_step": alg_bytes, "achieved_gbs": alg_bytes / (ms / 1e3) / 1e9,
                 "peak_gbs": hbm_peak, "frac": alg_bytes / (ms / 1e3) / 1e9 / hbm_peak, "peak_source": src}
@@ -439,6 +449,7 @@ def run_ours(args, rank, world):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"volume-{N} ({S} slices x {V} angles x {N} rays FP32, pad {alpha}, M={M})",
+                       "gridding": f"kaiser-bessel W={kbw}" if kbw else "bilinear",
                        "slices_per_gpu": S, "l2": "inputs (%.1f GiB) larger than L2" % (S * V * N * 4 / 2**30),
                        "parallelism": f"slices, {world} GPU(s), weak"},
             "slices_per_s": world * S / (ms / 1e3),
@@ -465,6 +476,9 @@ def main():
     ap.add_argument("--e2e-slices", type=int, default=2048)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the ragged-batch and autograd lines")
+    ap.add_argument("--gridding", default="bilinear", choices=["bilinear", "kb"],
+                    help="interpolation kernel of stage P5 for the main step (kb: Kaiser-Bessel)")
+    ap.add_argument("--kb-width", type=int, default=6)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
