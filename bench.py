@@ -82,9 +82,9 @@ STAGE_NAMES = {0: "k_ray_fft", 1: "k_grid_col", 2: "k_row_ifft", 3: "k_ss_filter
 KERNEL_SOURCES = ["paper_1704_08364_gb300/csrc/fbp.cu", "paper_1704_08364_gb300/csrc/bst_stages.cuh",
                   "paper_1704_08364_gb300/csrc/bst_fft.cuh", "paper_1704_08364_gb300/csrc/bst_geo.cuh"]
 CAPTURED_TRAFFIC = {
-    "sha": "4046076512adea6df2ad3344bbeb70afe855f0e99a4fcb248366e797b682217a",
+    "sha": "b7a54194759cd1670b4462241c89431736442e56ecb183fd19091ee08bf1b80c",
     "rays": 2048, "pad": 2,
-    "bytes": {"k_ray_fft": 33612800 + 10714624, "k_grid_col": 169022208 + 45011712, "k_row_ifft": 67150336 + 4470016},
+    "bytes": {"k_ray_fft": 33611776 + 9665792, "k_grid_col": 168354816 + 41901056, "k_row_ifft": 67152896 + 4591360},
 }
 
 

@@ -200,6 +200,37 @@ __device__ __forceinline__ void twiddles(const float2* __restrict__ tw, int b, f
     }
 }
 
+// a[s] *= w[s] (conjugated for the inverse) with w[s] = tw[s * b].  For R = 16
+// the upper half is applied as (w[s] w[8]) a[8 + s], the same products as the
+// table of twiddles() but never more than eight twiddles live at once.
+template <int R, bool INV>
+__device__ __forceinline__ void apply_twiddles(const float2* __restrict__ tw, int b, float2* a) {
+    if constexpr (R == 16) {
+        float2 w[8];
+        w[1] = __ldg(tw + b);
+        w[2] = __ldg(tw + 2 * b);
+        w[4] = __ldg(tw + 4 * b);
+        w[3] = cmul(w[1], w[2]);
+        w[5] = cmul(w[1], w[4]);
+        w[6] = cmul(w[2], w[4]);
+        w[7] = cmul(w[3], w[4]);
+#pragma unroll
+        for (int s = 1; s < 8; ++s) a[s] = INV ? cmulc(a[s], w[s]) : cmul(a[s], w[s]);
+        const float2 w8 = __ldg(tw + 8 * b);
+        a[8] = INV ? cmulc(a[8], w8) : cmul(a[8], w8);
+#pragma unroll
+        for (int s = 1; s < 8; ++s) {
+            const float2 ws = cmul(w[s], w8);
+            a[8 + s] = INV ? cmulc(a[8 + s], ws) : cmul(a[8 + s], ws);
+        }
+    } else {
+        float2 w[R];
+        twiddles<R>(tw, b, w);
+#pragma unroll
+        for (int s = 1; s < R; ++s) a[s] = INV ? cmulc(a[s], w[s]) : cmul(a[s], w[s]);
+    }
+}
+
 template <int M, int R, int NS, int TPL, bool INV, class Src, class Dst>
 __device__ __forceinline__ void stockham_pass(int t, const Src& src, const Dst& dst,
                                               const float2* __restrict__ tw, bool sync_mid) {
@@ -222,10 +253,7 @@ __device__ __forceinline__ void stockham_pass(int t, const Src& src, const Dst& 
             const int k = (NS == 1) ? 0 : (j % NS);
             if (NS > 1) {
                 constexpr int STEP = M / (NS * R);
-                float2 w[R];
-                twiddles<R>(tw, k * STEP, w);
-#pragma unroll
-                for (int s = 1; s < R; ++s) a[it][s] = INV ? cmulc(a[it][s], w[s]) : cmul(a[it][s], w[s]);
+                apply_twiddles<R, INV>(tw, k * STEP, a[it]);
             }
             Dft<R, INV>::run(a[it]);
             const int base = (j / NS) * NS * R + k;
