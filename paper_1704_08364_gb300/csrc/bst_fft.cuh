@@ -157,11 +157,17 @@ __host__ __device__ constexpr int smem_line_len(int M) { return M + M / 16; }
 struct SmemLine {
     float2* p;
     static constexpr bool kSmem = true;
+    static constexpr bool kPlain = true;   // load/store are exactly p[i + i/16]
     __device__ __forceinline__ float2 load(int i) const { return p[i + (i >> 4)]; }
     __device__ __forceinline__ void store(int i, float2 v) const { p[i + (i >> 4)] = v; }
 };
 
 // ---- passes ----------------------------------------------------------------
+
+// true for a plain SmemLine (no weighting or remapping in load/store)
+template <class T, class = void> struct plain_line_trait { static constexpr bool value = false; };
+template <class T> struct plain_line_trait<T, decltype(void(T::kPlain))> { static constexpr bool value = T::kPlain; };
+template <class T> __host__ __device__ constexpr bool is_plain_line() { return plain_line_trait<T>::value; }
 
 // w[s] = tw[s * b] for s = 1..R-1 (b = k M / (NS R)): the powers of two of the
 // base root come from the table, the others are products of at most three
@@ -241,8 +247,15 @@ __device__ __forceinline__ void stockham_pass(int t, const Src& src, const Dst& 
     for (int it = 0; it < IT; ++it) {
         const int j = t + it * TPL;
         if ((NB % TPL) == 0 || j < NB) {
+            if constexpr (is_plain_line<Src>() && NB % 16 == 0) {
+                // padded index of j + s NB is (j + j/16) + s (NB + NB/16): one base, constant offsets
+                const float2* p = src.p + j + (j >> 4);
 #pragma unroll
-            for (int s = 0; s < R; ++s) a[it][s] = src.load(j + s * NB);
+                for (int s = 0; s < R; ++s) a[it][s] = p[s * (NB + NB / 16)];
+            } else {
+#pragma unroll
+                for (int s = 0; s < R; ++s) a[it][s] = src.load(j + s * NB);
+            }
         }
     }
     if (sync_mid) __syncthreads();
@@ -257,8 +270,17 @@ __device__ __forceinline__ void stockham_pass(int t, const Src& src, const Dst& 
             }
             Dft<R, INV>::run(a[it]);
             const int base = (j / NS) * NS * R + k;
+            if constexpr (is_plain_line<Dst>() && (NS % 16 == 0 || (NS == 1 && 16 % R == 0))) {
+                // the R outputs base + s NS stay in one 16-group (NS = 1, base a multiple
+                // of R) or move by whole groups (NS a multiple of 16): constant offsets
+                float2* p = dst.p + base + (base >> 4);
+                constexpr int PS = NS == 1 ? 1 : NS + NS / 16;
 #pragma unroll
-            for (int s = 0; s < R; ++s) dst.store(base + s * NS, a[it][s]);
+                for (int s = 0; s < R; ++s) p[s * PS] = a[it][s];
+            } else {
+#pragma unroll
+                for (int s = 0; s < R; ++s) dst.store(base + s * NS, a[it][s]);
+            }
         }
     }
 }

@@ -159,3 +159,17 @@ def test_volume_2048_sampled_pixels_against_the_direct_sum(bst):
         scale = float(np.abs(got[n]).max())
         err = np.abs(got[n][rows, cols] - ref).max()
         assert err <= 2e-5 * scale, f"slice {s}: max err {err:.3e} vs scale {scale:.3e}"
+
+
+def test_host_pipeline_and_noalloc_on_a_kb_plan(bst):
+    """bst_fbp_host and bst_fbp_noalloc run the plan's KB gridding too."""
+    rng = np.random.default_rng(31)
+    N = V = 512
+    theta = synth.uniform_angles(V)
+    sino = np.stack([synth.ellipse_sinogram(synth.random_ellipses(rng), theta, N) for _ in range(3)]).astype(np.float32)
+    plan = bst.Plan(N, theta, 2)
+    plan.set_gridding("kaiser-bessel", 6)
+    ref = _oracle(sino, theta)
+    h = torch.from_numpy(sino).pin_memory()
+    assert_parity(plan.fbp_host(h).numpy(), ref, what="KB host pipeline")
+    assert_parity(plan.fbp_noalloc(torch.from_numpy(sino).cuda()).cpu().numpy(), ref, what="KB noalloc")
