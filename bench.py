@@ -82,9 +82,9 @@ STAGE_NAMES = {0: "k_ray_fft", 1: "k_grid_col", 2: "k_row_ifft", 3: "k_ss_filter
 KERNEL_SOURCES = ["paper_1704_08364_gb300/csrc/fbp.cu", "paper_1704_08364_gb300/csrc/bst_stages.cuh",
                   "paper_1704_08364_gb300/csrc/bst_fft.cuh", "paper_1704_08364_gb300/csrc/bst_geo.cuh"]
 CAPTURED_TRAFFIC = {
-    "sha": "b7a54194759cd1670b4462241c89431736442e56ecb183fd19091ee08bf1b80c",
+    "sha": "09a3c27da34b0bc49e3230fe240ddc4e098d7c19a866625c8eba004fe734f717",
     "rays": 2048, "pad": 2,
-    "bytes": {"k_ray_fft": 33611776 + 9665792, "k_grid_col": 168354816 + 41901056, "k_row_ifft": 67152896 + 4591360},
+    "bytes": {"k_ray_fft": 33609472 + 9562880, "k_grid_col": 167624192 + 39220736, "k_row_ifft": 67151360 + 4377088},
 }
 
 
