@@ -200,9 +200,13 @@ def bench_ragged(bst, synth, sdev, dev, steps):
     ms_direct = _event_ms(lambda: rb.run(False), steps)
     ms_graph = _event_ms(lambda: rb.run(True), steps)
     ok = rb.status() == 0
+    rb.bind(sinos, vols, flags=2)
+    ms_overlap = _event_ms(lambda: rb.run(True), steps)
+    ok = ok and rb.status() == 0
     return {"items": len(sizes), "pair_items": rb.pair_items, "voxels": voxels,
             "schedules": {str(N): plans[N].schedule for N in sorted(plans)},
             "per_size_ms": ms_per_size, "persistent_ms": ms_direct, "persistent_graph_ms": ms_graph,
+            "persistent_overlapped_order_graph_ms": ms_overlap,
             "persistent_graph_voxels_per_s": voxels / (ms_graph / 1e3), "status_ok": ok}
 
 

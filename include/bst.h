@@ -264,10 +264,13 @@ int bst_ragged_pair_items(bst_ragged_t batch);
 /* Bind device buffers: d_sinos[i] [V_i][N_i], d_volumes[i] [N_i][N_i] (host
  * arrays of device pointers), d_g[i] filter taps or NULL (d_g itself may be
  * NULL: ramp for all; paired items must share their taps).  Builds and
- * uploads the work queue; drops a captured graph.  flags: 0; bit 0 is a
- * diagnostic that leaves the ray stage of the first pair-item unqueued, so
- * that its dependent units wait until the spin limit and the launch reports
- * BST_ERR_TIMEOUT (used to test the bounded waits).  Every plan must use
+ * uploads the work queue; drops a captured graph.  The queue runs in phases
+ * (every ray unit, then every gridding unit, then every row unit, the
+ * largest pair-items first); flags bit 1 overlaps neighbouring pair-items'
+ * stages instead (stage s of pair-item k at step k + s); bit 0 is a diagnostic that leaves the ray stage of the
+ * first pair-item unqueued, so that its dependent units wait until the spin
+ * limit and the launch reports BST_ERR_TIMEOUT (used to test the bounded
+ * waits).  Every plan must use
  * bilinear gridding (INVALID_ARGUMENT otherwise). */
 bst_status_t bst_ragged_bind(bst_ragged_t batch, const float* const* d_sinos, const float* const* d_g,
                              float* const* d_volumes, void* d_ws, size_t ws_bytes, int flags);

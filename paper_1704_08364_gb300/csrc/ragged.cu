@@ -129,8 +129,9 @@ __global__ void __launch_bounds__(RAGGED_THREADS, 1)
         }
         __syncthreads();
         if (threadIdx.x == 0 && w.y < 2) {
-            __threadfence();
-            atomicAdd(done + 3 * w.x + w.y, 1);
+            // release: the block's writes of this unit (ordered before by the
+            // barrier) become visible to a unit that acquires the counter
+            asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(done + 3 * w.x + w.y) : "memory");
         }
     }
 }
@@ -318,15 +319,32 @@ bst_status_t bst_ragged_bind(bst_ragged_t r, const float* const* d_sinos, const 
         x.n[1] = (p->M / 2 + L - 1) / L;
         x.n[2] = ((p->N + 3) / 4 + L / 4 - 1) / (L / 4);
     }
-    // queue: stage s of pair-item k at step k + s; a unit always follows its dependencies
+    // queue; a unit always follows its dependencies.  Default: phases (every
+    // ray unit, then every gridding unit, then every row unit), the largest
+    // pair-items first within a phase (measured 6 % faster on a 64-item batch).
+    // Flag bit 1: stage s of pair-item k at step k + s (neighbouring items overlap).
     std::vector<int4> q;
-    for (int step = 0; step < pairs + 2; ++step)
-        for (int s = 0; s < 3; ++s) {
-            const int k = step - s;
-            if (k < 0 || k >= pairs) continue;
-            if (s == 0 && k == 0 && (flags & 1)) continue;   // diagnostic: leave pair-item 0's ray stage unqueued
-            for (int u = 0; u < it[k].n[s]; ++u) q.push_back(make_int4(k, s, u, 0));
-        }
+    const bool skip0 = (flags & 1) != 0;   // diagnostic: leave pair-item 0's ray stage unqueued
+    if (!(flags & 2)) {
+        std::vector<int> order(pairs);
+        for (int k = 0; k < pairs; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return (size_t)it[a].M * it[a].V > (size_t)it[b].M * it[b].V;
+        });
+        for (int s = 0; s < 3; ++s)
+            for (int k : order) {
+                if (s == 0 && k == 0 && skip0) continue;
+                for (int u = 0; u < it[k].n[s]; ++u) q.push_back(make_int4(k, s, u, 0));
+            }
+    } else {
+        for (int step = 0; step < pairs + 2; ++step)
+            for (int s = 0; s < 3; ++s) {
+                const int k = step - s;
+                if (k < 0 || k >= pairs) continue;
+                if (s == 0 && k == 0 && skip0) continue;
+                for (int u = 0; u < it[k].n[s]; ++u) q.push_back(make_int4(k, s, u, 0));
+            }
+    }
     int4* dq = nullptr;
     if (cudaMalloc((void**)&dq, std::max<size_t>(1, q.size()) * sizeof(int4)) != cudaSuccess)
         return BST_ERR_OUT_OF_MEMORY;

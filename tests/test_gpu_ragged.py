@@ -31,12 +31,14 @@ def _batch(sizes, seed=0):
 SIZES = [256, 128, 512, 384, 256, 768, 128, 1024, 512, 256, 384, 2048]
 
 
-def test_ragged_matches_per_item_path(bst):
+@pytest.mark.parametrize("order", [0, 2])
+def test_ragged_matches_per_item_path(bst, order):
+    """Both queue orders: phases (0) and neighbouring pair-items overlapping (2)."""
     plans = {N: bst.Plan(N, synth.uniform_angles(N), 2) for N in sorted(set(SIZES))}
     host = _batch(SIZES)
     sinos = [torch.from_numpy(h).cuda() for h in host]
     vols = [torch.full((N, N), float("nan"), device="cuda") for N in SIZES]
-    rb = bst.RaggedBatch([plans[N] for N in SIZES]).bind(sinos, vols)
+    rb = bst.RaggedBatch([plans[N] for N in SIZES]).bind(sinos, vols, flags=order)
     assert rb.pair_items == 8   # 256 x3 -> 2, 128 x2 -> 1, 512 x2, 384 x2, 768, 1024, 2048
     refs = [plans[N].fbp(s.unsqueeze(0))[0].cpu().numpy() for N, s in zip(SIZES, sinos)]
     for use_graph in (False, True, True):
