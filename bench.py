@@ -406,9 +406,12 @@ def run_ours(args, rank, world):
     hbm_peak, sm_max, src = _peaks()
     peak_tf = fp32_peak_tflops(sm_max)
     achieved_tf = flops[dom] / (avg_ms / 1e3) / 1e12
+    traffic = None if kbw else captured_traffic(names[dom], N, alpha)
     roofline = {"bound": "alu", "kernel": names[dom], "achieved": achieved_tf, "peak": peak_tf,
                 "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
-                "traffic": None if kbw else captured_traffic(names[dom], N, alpha),
+                "traffic": traffic,
+                "dram_gbs": None if traffic is None else traffic / (avg_ms / 1e3) / 1e9,
+                "dram_frac_of_hbm_peak": None if traffic is None else traffic / (avg_ms / 1e3) / 1e9 / hbm_peak,
                 "traffic_note": "DRAM bytes per launch from one cold-cache ncu capture (null if the kernel changed)",
                 "algorithmic_flops_per_launch": flops[dom],
                 "peak_source": "FP32 152 SM x 128 lanes x 2 x %.0f MHz (derived)" % sm_max,
