@@ -334,16 +334,20 @@ def run_ours(args, rank, world):
     plan.status()
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with ClockSampler(dev.index) as clk:
         barrier()
         torch.cuda.synchronize()
         e0.record(st)
-        for _ in range(args.steps):
+        marks[0].record(st)
+        for k in range(args.steps):
             plan.fbp(sino, out=vol)
+            marks[k + 1].record(st)
         e1.record(st)
         torch.cuda.synchronize()
         barrier()
     ms = e0.elapsed_time(e1) / args.steps
+    step_ms = [marks[k].elapsed_time(marks[k + 1]) for k in range(args.steps)]
     plan.status()
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -453,7 +457,8 @@ def run_ours(args, rank, world):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "median_step_ms": statistics.median(step_ms),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"volume-{N} ({S} slices x {V} angles x {N} rays FP32, pad {alpha}, M={M})",
                        "gridding": f"kaiser-bessel W={kbw}" if kbw else "bilinear",

@@ -95,12 +95,13 @@ def test_volume_512_sampled_slices(bst):
 
 def test_volume_2048_sampled_slices(bst):
     """The 2048 x 2048 x 2048 workload in the benchmark's launch configuration
-    (one slice pair per chunk, 1024 chunks): sampled slices, regenerated on the
-    host, against the oracle."""
+    (one slice pair per chunk, 1024 chunks): eight seeded slices (both halves of
+    the first and last pairs and of the pairs around the middle), regenerated on
+    the host, against the oracle."""
     free, _ = torch.cuda.mem_get_info()
     if free < 72 * 2**30:
         pytest.skip("needs ~70 GiB of free device memory")
-    idx = [0, 1, 2047]
+    idx = [0, 1, 2, 3, 1023, 1024, 2046, 2047]
     theta, sub, _ = synth.workload_slices("volume-2048", idx)
     plan = bst.Plan(2048, theta, 2)
     d = torch.zeros((2048, 2048, 2048), dtype=torch.float32, device="cuda")
