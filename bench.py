@@ -79,7 +79,7 @@ STAGE_NAMES = {0: "k_ray_fft", 1: "k_grid_col", 2: "k_row_ifft", 3: "k_ss_filter
 # DRAM bytes (read + write) per launch from one `ncu --set full` capture of
 # each forward kernel (profiles/k_fwd_volume-2048.md), valid only while the
 # kernel sources hash to `sha`; otherwise the roofline reports traffic null.
-KERNEL_SOURCES = ["paper_1704_08364_gb300/csrc/fbp.cu", "paper_1704_08364_gb300/csrc/bst_stages.cuh",
+KERNEL_SOURCES = ["paper_1704_08364_gb300/csrc/bst_forward.cuh", "paper_1704_08364_gb300/csrc/bst_stages.cuh",
                   "paper_1704_08364_gb300/csrc/bst_fft.cuh", "paper_1704_08364_gb300/csrc/bst_geo.cuh"]
 CAPTURED_TRAFFIC = {
     "sha": "09a3c27da34b0bc49e3230fe240ddc4e098d7c19a866625c8eba004fe734f717",

@@ -17,7 +17,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
 LIBS = {
-    "bst": (os.path.join(HERE, "csrc"), ["plan.cu", "fbp.cu", "adjoint.cu", "brute.cu", "noalloc.cu", "host.cu", "ragged.cu", "kb.cu"],
+    "bst": (os.path.join(HERE, "csrc"), ["plan.cu", "fbp.cu", "adjoint.cu", "brute.cu", "noalloc.cu", "host.cu", "ragged.cu", "kb.cu", "fbp_pad1.cu", "fbp_pad2.cu"],
             os.path.join(HERE, "libbst.so")),
     "bstsynth": (os.path.join(ROOT, "synth", "csrc"), ["synth.cu"],
                  os.path.join(ROOT, "synth", "libbstsynth.so")),

@@ -164,6 +164,28 @@ struct SmemLine {
 
 // ---- passes ----------------------------------------------------------------
 
+// Sources that know index groups of always-zero input (S::zero_group) and
+// destinations that know index groups of outputs they drop (D::drop_group):
+// the first pass then loads nothing there and the last pass stores nothing
+// there, and the compiler removes the arithmetic that only fed them.
+template <class T, class = void> struct zero_group_trait { static constexpr bool value = false; };
+template <class T>
+struct zero_group_trait<T, decltype(void(T::zero_group(0, 0, 0)))> { static constexpr bool value = true; };
+template <class T, class = void> struct drop_group_trait { static constexpr bool value = false; };
+template <class T>
+struct drop_group_trait<T, decltype(void(T::drop_group(0, 0, 0)))> { static constexpr bool value = true; };
+
+template <class S, int M>
+__device__ __forceinline__ constexpr bool src_zero_group(int lo, int hi) {
+    if constexpr (zero_group_trait<S>::value) return S::zero_group(lo, hi, M);
+    return false;
+}
+template <class D, int M>
+__device__ __forceinline__ constexpr bool dst_drop_group(int lo, int hi) {
+    if constexpr (drop_group_trait<D>::value) return D::drop_group(lo, hi, M);
+    return false;
+}
+
 // true for a plain SmemLine (no weighting or remapping in load/store)
 template <class T, class = void> struct plain_line_trait { static constexpr bool value = false; };
 template <class T> struct plain_line_trait<T, decltype(void(T::kPlain))> { static constexpr bool value = T::kPlain; };
@@ -254,7 +276,9 @@ __device__ __forceinline__ void stockham_pass(int t, const Src& src, const Dst& 
                 for (int s = 0; s < R; ++s) a[it][s] = p[s * (NB + NB / 16)];
             } else {
 #pragma unroll
-                for (int s = 0; s < R; ++s) a[it][s] = src.load(j + s * NB);
+                for (int s = 0; s < R; ++s)
+                    a[it][s] = src_zero_group<Src, M>(s * NB, (s + 1) * NB) ? make_float2(0.f, 0.f)
+                                                                              : src.load(j + s * NB);
             }
         }
     }
@@ -278,8 +302,11 @@ __device__ __forceinline__ void stockham_pass(int t, const Src& src, const Dst& 
 #pragma unroll
                 for (int s = 0; s < R; ++s) p[s * PS] = a[it][s];
             } else {
+                // in the last pass base = j < NS, so output s covers indices [s NS, (s + 1) NS)
+                constexpr bool LASTP = NS * R == M;
 #pragma unroll
-                for (int s = 0; s < R; ++s) dst.store(base + s * NS, a[it][s]);
+                for (int s = 0; s < R; ++s)
+                    if (!(LASTP && dst_drop_group<Dst, M>(s * NS, (s + 1) * NS))) dst.store(base + s * NS, a[it][s]);
             }
         }
     }

@@ -122,6 +122,11 @@ struct PrepArgs;
 // as bst_launch_forward (filter mode) with the pre-reconstruction stages in the ray kernel
 bst_status_t bst_launch_forward_prep(bst_plan_s* p, const float* sino, int slices, const bst::PrepArgs& prep,
                                      const float* g, float* vol, void* ws, size_t ws_bytes, cudaStream_t st);
+// the forward path for pad factor 1 or 2 (fbp_pad1.cu, fbp_pad2.cu); prep may be null
+bst_status_t bst_forward_pad1(bst_plan_s* p, const float* sino, int slices, int mode, const float* g, float* vol,
+                              void* ws, cudaStream_t st, int max_chunk, int lanes, const bst::PrepArgs* prep);
+bst_status_t bst_forward_pad2(bst_plan_s* p, const float* sino, int slices, int mode, const float* g, float* vol,
+                              void* ws, cudaStream_t st, int max_chunk, int lanes, const bst::PrepArgs* prep);
 // create the plan's two chunk streams and their events (false on failure)
 bool bst_ensure_lanes(bst_plan_s* p);
 bst_status_t bst_launch_adjoint(bst_plan_s* p, int mode, const float* g, const float* vol, int slices,

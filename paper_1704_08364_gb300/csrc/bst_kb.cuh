@@ -216,7 +216,7 @@ __device__ __forceinline__ void kb_col_unit(float2* smem, int strip, int V, int 
     // inverse FFT along r' of each column in place; the N central rows go to T
     const int line = tid / TPL, t = tid % TPL;
     const SmemLine sm{smem + line * LL};
-    const ColDst dst{Tp, N, M, c0 + line, false, true};
+    const ColDst<> dst{Tp, N, M, c0 + line, false, true};
     fft_line<M, TPL, true, MAXR>(t, sm, dst, sm, tw);
 }
 

@@ -28,16 +28,24 @@ namespace bst {
 // threads per line: 16 elements per thread (12 for lengths 3 * 2^a)
 template <int M> __host__ __device__ constexpr int tpl_of() { return (M % 3 == 0) ? M / 12 : M / 16; }
 
+// NC: the ray count N as a compile-time constant (0: the runtime value).  With
+// it, the padded samples that are always zero are known per index group.
+template <int NC = 0>
 struct RaySrc {
     const float* ya;
     const float* yb;
     int N, M;
     bool live;
     static constexpr bool kSmem = false;
+    // every padded index m in [lo, hi) lies in the zero padding
+    static __host__ __device__ constexpr bool zero_group(int lo, int hi, int Mc) {
+        return NC > 0 && lo >= NC / 2 && hi <= Mc - NC / 2;
+    }
     __device__ __forceinline__ float2 load(int m) const {
-        int i = m + (N >> 1);
+        const int n = NC > 0 ? NC : N;
+        int i = m + (n >> 1);
         if (i >= M) i -= M;
-        if (!live || i >= N) return make_float2(0.f, 0.f);
+        if (!live || i >= n) return make_float2(0.f, 0.f);
         return make_float2(__ldg(ya + i), yb ? __ldg(yb + i) : 0.f);
     }
 };
@@ -66,16 +74,22 @@ struct SpecDst {
 // T layout per pair: [ceil(N/4)][M][4] complex, row r of the kept band at
 // (r / 4, c', r % 4): a column write fills whole 32-byte sectors and a
 // four-row block is contiguous for k_row_ifft.
+template <int NC = 0>
 struct ColDst {
     float2* T;
     int N, M, cidx;
     bool rev, live;
     static constexpr bool kSmem = false;
+    // no output index p in [lo, hi) is kept (in either reading direction)
+    static __host__ __device__ constexpr bool drop_group(int lo, int hi, int Mc) {
+        return NC > 0 && lo >= NC / 2 + 1 && hi <= Mc - NC / 2;
+    }
     __device__ __forceinline__ void store(int p, float2 v) const {
         if (!live) return;
+        const int n = NC > 0 ? NC : N;
         const int q = rev ? (p == 0 ? 0 : M - p) : p;
-        const int r = signed_freq(q, M) + (N >> 1);
-        if (r < 0 || r >= N) return;
+        const int r = signed_freq(q, M) + (n >> 1);
+        if (r < 0 || r >= n) return;
         T[((size_t)(r >> 2) * M + cidx) * 4 + (r & 3)] = v;
     }
 };
@@ -197,6 +211,7 @@ struct TileSrc {
     }
 };
 
+template <int NC = 0>
 struct VolDst {
     float* va;
     float* vb;
@@ -205,10 +220,15 @@ struct VolDst {
     bool live;
     const float* dk;    // per-column deapodization of KB gridding, or null
     static constexpr bool kSmem = false;
+    // no output index p in [lo, hi) falls inside the N kept columns
+    static __host__ __device__ constexpr bool drop_group(int lo, int hi, int Mc) {
+        return NC > 0 && lo >= NC / 2 && hi <= Mc - NC / 2;
+    }
     __device__ __forceinline__ void store(int p, float2 v) const {
         if (!live) return;
-        const int c = signed_freq(p, M) + (N >> 1);
-        if (c < 0 || c >= N) return;
+        const int n = NC > 0 ? NC : N;
+        const int c = signed_freq(p, M) + (n >> 1);
+        if (c < 0 || c >= n) return;
         const float s = dk ? scale * __ldg(dk + c) : scale;
         va[c] = v.x * s;
         if (vb) vb[c] = v.y * s;
@@ -236,6 +256,7 @@ struct PrepArgs {
     float kb_norm;        // 1 / I0(kb_beta)
 };
 
+template <int NC = 0>
 struct RaySrcPrep {
     const float* ya;
     const float* yb;
@@ -247,6 +268,9 @@ struct RaySrcPrep {
     bool live;
     PrepArgs pa;
     static constexpr bool kSmem = false;
+    static __host__ __device__ constexpr bool zero_group(int lo, int hi, int Mc) {
+        return NC > 0 && lo >= NC / 2 && hi <= Mc - NC / 2;
+    }
     __device__ __forceinline__ float sample(const float* y, const float* d, const float* f, int i) const {
         float v = __ldg(y + i);
         if (f) {
@@ -256,12 +280,13 @@ struct RaySrcPrep {
         return v;
     }
     __device__ __forceinline__ float2 load(int m) const {
-        int i = m + (N >> 1);
+        const int n = NC > 0 ? NC : N;
+        int i = m + (n >> 1);
         if (i >= M) i -= M;
-        if (!live || i >= N) return make_float2(0.f, 0.f);
+        if (!live || i >= n) return make_float2(0.f, 0.f);
         float w = 1.f;
         if (pa.kb_beta > 0.f) {
-            const float t = ((float)(i - (N >> 1)) - pa.shift) * (2.f / (float)N);
+            const float t = ((float)(i - (n >> 1)) - pa.shift) * (2.f / (float)n);
             const float u = t * pa.kb_inv_half;
             w = fabsf(u) <= 1.f ? cyl_bessel_i0f(pa.kb_beta * sqrtf(fmaxf(1.f - u * u, 0.f))) * pa.kb_norm : 0.f;
         }
@@ -303,7 +328,7 @@ struct SpecDstShift {
 
 // ray_unit with the pre-reconstruction stages (slice rows da/db, fa/fb of the
 // dark and flat fields, or null)
-template <int M, int TPL, int LPC, int MAXR>
+template <int M, int TPL, int LPC, int MAXR, int NC = 0>
 __device__ __forceinline__ void ray_unit_prep(float2* smem, int j0, int V, int N, const float* __restrict__ ya,
                                               const float* __restrict__ yb, const float* da, const float* db,
                                               const float* fa, const float* fb, const PrepArgs& pa, int mode,
@@ -313,14 +338,14 @@ __device__ __forceinline__ void ray_unit_prep(float2* smem, int j0, int V, int N
     const int j = j0 + line;
     const bool live = j < V;
     const int jj = live ? j : 0;
-    RaySrcPrep src{ya + (size_t)jj * N, yb ? yb + (size_t)jj * N : nullptr, da, db, fa, fb, N, M, live, pa};
+    RaySrcPrep<NC> src{ya + (size_t)jj * N, yb ? yb + (size_t)jj * N : nullptr, da, db, fa, fb, N, M, live, pa};
     SpecDstShift dst{Zp + (size_t)jj * M, g, M, mode, two_alpha, live, pa};
     SmemLine sm{smem + line * smem_line_len(M)};
     fft_line<M, TPL, false, MAXR>(t, src, dst, sm, tw);
 }
 
 // P2 + P3 + P4 for lines j0 .. j0 + LPC - 1 of one slice pair (blockDim = TPL * LPC)
-template <int M, int TPL, int LPC, int MAXR>
+template <int M, int TPL, int LPC, int MAXR, int NC = 0>
 __device__ __forceinline__ void ray_unit(float2* smem, int j0, int V, int N, const float* __restrict__ ya,
                                          const float* __restrict__ yb, int mode, const float* __restrict__ g,
                                          float two_alpha, float2* __restrict__ Zp, const float2* __restrict__ tw) {
@@ -328,7 +353,7 @@ __device__ __forceinline__ void ray_unit(float2* smem, int j0, int V, int N, con
     const int j = j0 + line;
     const bool live = j < V;
     const int jj = live ? j : 0;
-    RaySrc src{ya + (size_t)jj * N, yb ? yb + (size_t)jj * N : nullptr, N, M, live};
+    RaySrc<NC> src{ya + (size_t)jj * N, yb ? yb + (size_t)jj * N : nullptr, N, M, live};
     SpecDst dst{Zp + (size_t)jj * M, g, M, mode, two_alpha, live};
     SmemLine sm{smem + line * smem_line_len(M)};
     fft_line<M, TPL, false, MAXR>(t, src, dst, sm, tw);
@@ -339,7 +364,7 @@ __device__ __forceinline__ void ray_unit(float2* smem, int j0, int V, int N, con
 // index-reversed, its transform is read back reversed; column -M/2 pairs with
 // q = 0 and is zero).  Consecutive lanes take consecutive rows, so a warp's taps
 // fall on neighbouring polar samples.
-template <int M, int TPL, int CPC, int MAXR>
+template <int M, int TPL, int CPC, int MAXR, int NC = 0>
 __device__ __forceinline__ void grid_unit(float2* smem, int q0, int V, int N, const float2* __restrict__ Zp,
                                           const int* __restrict__ gJ, const float2* __restrict__ gF,
                                           float2* __restrict__ Tp, const float2* __restrict__ tw) {
@@ -389,7 +414,7 @@ __device__ __forceinline__ void grid_unit(float2* smem, int q0, int V, int N, co
             }
         }
         __syncthreads();
-        const ColDst dst{Tp, N, M, side == 0 ? q : (q == 0 ? (M >> 1) : M - q), side == 1 && q != 0, live};
+        const ColDst<NC> dst{Tp, N, M, side == 0 ? q : (q == 0 ? (M >> 1) : M - q), side == 1 && q != 0, live};
         fft_line<M, TPL, true, MAXR>(t, sm, dst, sm, tw);
         __syncthreads();
     }
@@ -397,7 +422,7 @@ __device__ __forceinline__ void grid_unit(float2* smem, int q0, int V, int N, co
 
 // row P6 + P7 + P8 for row blocks rb0 .. rb0 + TPC - 1 of four rows (blockDim = 4 TPL TPC);
 // va, vb: the [N][N] images of slices a and b (vb may be null)
-template <int M, int TPL, int TPC, int MAXR>
+template <int M, int TPL, int TPC, int MAXR, int NC = 0>
 __device__ __forceinline__ void row_unit(float2* smem, int rb0, int N, const float2* __restrict__ Tp,
                                          float* __restrict__ va, float* __restrict__ vb, float scale,
                                          const float2* __restrict__ tw, const float* __restrict__ dk = nullptr) {
@@ -409,7 +434,7 @@ __device__ __forceinline__ void row_unit(float2* smem, int rb0, int N, const flo
     const bool live = r < N;
     const int rr = live ? r : 0;
     TileSrc src{Tp, M, live ? rb : 0, line, live};
-    VolDst dst{va + (size_t)rr * N, vb ? vb + (size_t)rr * N : nullptr, N, M,
+    VolDst<NC> dst{va + (size_t)rr * N, vb ? vb + (size_t)rr * N : nullptr, N, M,
                dk ? scale * __ldg(dk + rr) : scale, live, dk};
     SmemLine sm{smem + (tile * 4 + line) * row_line_stride<M>()};
     fft_line<M, TPL, true, MAXR>(t, src, dst, sm, tw);
