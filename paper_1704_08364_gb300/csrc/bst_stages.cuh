@@ -1,6 +1,6 @@
 // bst_stages.cuh -- the three stages of the BST forward path as device
 // functions over "units" (a few lines of one slice pair), shared by the
-// per-size kernels of fbp.cu and the persistent ragged kernel of ragged.cu.
+// per-size kernels of bst_forward.cuh and the persistent ragged kernel of ragged.cu.
 //
 //   ray_unit   stages P2 + P3 + P4 for LPC angles j0.. of a pair: centre-aligned
 //              zero padding of the rays to M, forward FFT along t, weight W[|k|],

@@ -1,5 +1,5 @@
 // plan.cu -- plan creation (device tables), argument validation and the
-// public entry points of libbst.  The kernels live in fbp.cu (forward BST),
+// public entry points of libbst.  The kernels live in bst_forward.cuh (forward BST),
 // adjoint.cu (Fourier-slice adjoint and filter gradient) and brute.cu
 // (slant-stack comparator).
 #include <cuda_runtime.h>
