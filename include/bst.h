@@ -152,6 +152,21 @@ bst_status_t bst_fbp_filter_grad(bst_plan_t plan, const float* d_sino,
                                  float* d_grad_g, void* d_ws, size_t ws_bytes,
                                  bst_stream_t stream);
 
+/* Backward of x = FBP(sino; g) for autograd: both gradients of
+ * <grad_vol, x> from one polar pull-back of grad_vol per chunk of slices.
+ *   d_grad_sino [slices][V][N]: the adjoint applied to grad_vol (as
+ *               radon_adjoint, mode FILTER, taps d_g), or NULL to skip;
+ *   d_grad_g    [M/2]: as bst_fbp_filter_grad (overwritten), or NULL to skip
+ *               (then d_sino may be NULL).
+ * Results equal those of the two separate calls.  Workspace:
+ * bst_adjoint_workspace_bytes.  A plan with KB gridding is rejected.
+ * Errors: INVALID_ARGUMENT (nothing requested, aliasing), WORKSPACE_TOO_SMALL,
+ * CUDA, OUT_OF_MEMORY. */
+bst_status_t bst_fbp_backward(bst_plan_t plan, const float* d_sino,
+                              const float* d_grad_vol, int slices, const float* d_g,
+                              float* d_grad_sino, float* d_grad_g, void* d_ws,
+                              size_t ws_bytes, bst_stream_t stream);
+
 /* Device workspace in bytes for brute_backproject with a filter (0 without). */
 size_t brute_workspace_bytes(bst_plan_t plan, int slices, int filtered);
 

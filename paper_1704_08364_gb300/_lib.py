@@ -38,6 +38,7 @@ SIGNATURES = {
     "bst_noalloc_scratch_bytes": (c_size, []),
     "bst_plan_set_schedule": (c_int, [c_plan, c_int]),
     "bst_plan_get_schedule": (c_int, [c_plan]),
+    "bst_fbp_backward": (c_int, [c_plan, c_ptr, c_ptr, c_int, c_ptr, c_ptr, c_ptr, c_ptr, ctypes.c_size_t, c_ptr]),
     "bst_plan_set_gridding": (c_int, [c_plan, c_int, c_int]),
     "bst_plan_get_gridding": (c_int, [c_plan, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "bst_plan_autotune": (c_int, [c_plan, c_int, ctypes.POINTER(c_int)]),

@@ -278,6 +278,25 @@ class Plan:
                                              ws.numel(), _stream()), "bst_fbp_filter_grad")
         return out
 
+    def fbp_backward(self, sino, grad_vol, g=None, want_sino: bool = True, want_g: bool = True):
+        """Both gradients of sum(grad_vol * fbp(sino, g)) from one polar pull-back
+        (bst_fbp_backward): (grad_sino [S][V][N] or None, grad_g [M/2] or None)."""
+        _need(grad_vol, "grad_vol")
+        S = grad_vol.shape[0]
+        _need(grad_vol, "grad_vol", (S, self.rays, self.rays))
+        if want_g:
+            _need(sino, "sino", (S, self.V, self.rays))
+        if g is not None:
+            _need(g, "g", (self.M // 2,))
+        dev = grad_vol.device
+        gs = torch.empty((S, self.V, self.rays), dtype=torch.float32, device=dev) if want_sino else None
+        gg = torch.empty((self.M // 2,), dtype=torch.float32, device=dev) if want_g else None
+        nb = self.adjoint_workspace_bytes(S)
+        ws = self.workspace("adj", nb, dev)
+        _check(self._lib.bst_fbp_backward(self._h, _ptr(sino if want_g else None), _ptr(grad_vol), S, _ptr(g),
+                                          _ptr(gs), _ptr(gg), _ptr(ws), ws.numel(), _stream()), "bst_fbp_backward")
+        return gs, gg
+
     def brute_backproject(self, sino, g=None, out=None):
         """Slant-stack backprojection (Eq. 2); with taps g, SS filtered backprojection."""
         _need(sino, "sino")
@@ -298,8 +317,9 @@ class Plan:
 
 class BstFbpFn(torch.autograd.Function):
     """x = FBP(p; g) with gradients for the sinogram p and the filter taps g.
-    Backward: grad_p = radon_adjoint(grad_x) (the Fourier-slice transpose),
-    grad_g = filter_grad(p, grad_x); FFT intermediates are recomputed."""
+    Backward (bst_fbp_backward): grad_p = radon_adjoint(grad_x) (the Fourier-slice
+    transpose) and grad_g = filter_grad(p, grad_x) from one polar pull-back of
+    grad_x; the FFT intermediates are recomputed, not stored."""
 
     @staticmethod
     def forward(ctx, sino, g, plan: Plan):
@@ -312,8 +332,10 @@ class BstFbpFn(torch.autograd.Function):
         sino, g = ctx.saved_tensors
         plan = ctx.plan
         gx = grad_x.contiguous()
-        gp = plan.radon_adjoint(gx, FILTER, g) if ctx.needs_input_grad[0] else None
-        gg = plan.filter_grad(sino, gx) if ctx.needs_input_grad[1] else None
+        want_p, want_g = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (want_p or want_g):
+            return None, None, None
+        gp, gg = plan.fbp_backward(sino.contiguous(), gx, g.contiguous(), want_p, want_g)
         return gp, gg, None
 
 

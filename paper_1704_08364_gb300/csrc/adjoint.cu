@@ -147,19 +147,35 @@ __device__ __forceinline__ float2 cell_sum(const Cells& cl, const float2* __rest
     return acc;
 }
 
+// Weighted sum over the cells (J, K0 - 1) (tap `hi`: its radial weight is fk)
+// and (J, K0) (tap `lo`: 1 - fk), which are adjacent in the cell lists, with
+// angular weight fth (rows J + 1 of the bracket) or 1 - fth (row J).
+__device__ __forceinline__ float2 cell_pair_sum(const Cells& cl, const float2* __restrict__ X, int M, int J, int K0,
+                                                bool upper) {
+    float2 acc = make_float2(0.f, 0.f);
+    const int cell = (J + 1) * M + (K0 + (M >> 1));
+    const int b = __ldg(cl.start + cell - 1), mid = __ldg(cl.start + cell), e = __ldg(cl.start + cell + 1);
+    for (int i = b; i < e; ++i) {
+        const float2 fw = __ldg(cl.w + i);
+        const float wt = (upper ? fw.x : 1.f - fw.x) * (i < mid ? fw.y : 1.f - fw.y);
+        const float2 x = __ldg(X + __ldg(cl.pts + i));
+        acc.x = fmaf(wt, x.x, acc.x);
+        acc.y = fmaf(wt, x.y, acc.y);
+    }
+    return acc;
+}
+
 // lambda_j[K]: transpose of the gridding (every cell tap that lands on (j, K))
 __device__ __forceinline__ float2 polar_pullback(const Cells& cl, const float2* __restrict__ X, int V, int M, int j,
                                                  int K) {
     float2 s = make_float2(0.f, 0.f);
     if (K <= -(M >> 1)) return s;
     float2 v;
-    v = cell_sum(cl, X, M, j, K, 0);
+    // taps (j, K) of the cells (j, K) [weight 1 - fk] and (j, K - 1) [weight fk], bracket row J = j
+    v = cell_pair_sum(cl, X, M, j, K, false);
     s.x += v.x; s.y += v.y;
-    v = cell_sum(cl, X, M, j, K - 1, 1);
-    s.x += v.x; s.y += v.y;
-    v = cell_sum(cl, X, M, j - 1, K, 2);
-    s.x += v.x; s.y += v.y;
-    v = cell_sum(cl, X, M, j - 1, K - 1, 3);
+    // the same from bracket J = j - 1, whose upper row J + 1 is j
+    v = cell_pair_sum(cl, X, M, j - 1, K, true);
     s.x += v.x; s.y += v.y;
     if (j == 0) {  // seam: the J+1 = V taps of bracket V-1 read row 0 at -k
         v = cell_sum(cl, X, M, V - 1, -K, 2);
@@ -193,7 +209,8 @@ struct SinoCrop {
 };
 
 // mode: BSTK_FILTER / BSTK_BACKPROJECT: weight, inverse FFT, crop -> sino;
-//       BSTK_RAW: write lambda (no weight) to lam[pair][V][M]
+//       BSTK_RAW: no sinogram.
+// lam (may be null in the first two modes): lambda (no weight) to lam[pair][V][M]
 template <int M, int TPL, int LPC>
 __global__ void __launch_bounds__(TPL * LPC)
     k_adj_polar(const float2* __restrict__ X, Cells cl, int V, int N, int slices, int pair0, int mode,
@@ -216,20 +233,15 @@ __global__ void __launch_bounds__(TPL * LPC)
                 v.x += origin.x / (float)V;
                 v.y += origin.y / (float)V;
             }
-            if (mode != BSTK_RAW) {
-                const int ak = k <= (M >> 1) ? k : M - k;
-                float w;
-                if (ak == (M >> 1)) w = 0.f;
-                else if (mode == BSTK_FILTER) w = g ? __ldg(g + ak) : 1.f;
-                else w = ak == 0 ? 0.f : __fdiv_rn(two_alpha, (float)ak);
-                v.x *= w;
-                v.y *= w;
-            }
         }
-        if (mode == BSTK_RAW) {
-            if (live) lam[((size_t)pl * V + jj) * M + k] = v;
-        } else {
-            sm.store(k, v);
+        if (lam && live) lam[((size_t)pl * V + jj) * M + k] = v;
+        if (mode != BSTK_RAW) {
+            const int ak = k <= (M >> 1) ? k : M - k;
+            float w;
+            if (ak == (M >> 1)) w = 0.f;
+            else if (mode == BSTK_FILTER) w = g ? __ldg(g + ak) : 1.f;
+            else w = ak == 0 ? 0.f : __fdiv_rn(two_alpha, (float)ak);
+            sm.store(k, make_float2(v.x * w, v.y * w));
         }
     }
     if (mode == BSTK_RAW) return;   // uniform across the block
@@ -266,19 +278,34 @@ __global__ void k_cell_keys(Geo geo, int M, int* __restrict__ key, float2* __res
 // filter gradient reductions
 
 // part[pair][k] = sum_j Re(conj(lam_j[k]) Y_j[k])
-__global__ void k_fg_partial(const float2* __restrict__ lam, const float2* __restrict__ Y, int V, int M,
-                             int pair0, float* __restrict__ part) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+// part[pair][k] = sum_j Re(conj(lam_j[k]) Y_j[k]): a block takes 32 bins k and
+// splits the angles over 8 groups of its threads (j = g, g + 8, ...), whose
+// sums are then added in a fixed order (deterministic)
+constexpr int FG_K = 32, FG_G = 8;
+__global__ void __launch_bounds__(FG_K * FG_G)
+    k_fg_partial(const float2* __restrict__ lam, const float2* __restrict__ Y, int V, int M, int pair0,
+                 float* __restrict__ part) {
+    __shared__ float red[FG_G][FG_K];
+    const int kl = threadIdx.x % FG_K, grp = threadIdx.x / FG_K;
+    const int k = blockIdx.x * FG_K + kl;
     const int pl = blockIdx.y;
-    if (k >= M) return;
-    const float2* l = lam + (size_t)pl * V * M + k;
-    const float2* y = Y + (size_t)pl * V * M + k;
     float s = 0.f;
-    for (int j = 0; j < V; ++j) {
-        const float2 a = __ldg(l + (size_t)j * M), b = __ldg(y + (size_t)j * M);
-        s = fmaf(a.x, b.x, fmaf(a.y, b.y, s));
+    if (k < M) {
+        const float2* l = lam + (size_t)pl * V * M + k;
+        const float2* y = Y + (size_t)pl * V * M + k;
+        for (int j = grp; j < V; j += FG_G) {
+            const float2 a = __ldg(l + (size_t)j * M), b = __ldg(y + (size_t)j * M);
+            s = fmaf(a.x, b.x, fmaf(a.y, b.y, s));
+        }
     }
-    part[(size_t)(pair0 + pl) * M + k] = s;
+    red[grp][kl] = s;
+    __syncthreads();
+    if (grp == 0 && k < M) {
+        float t = 0.f;
+#pragma unroll
+        for (int g = 0; g < FG_G; ++g) t += red[g][kl];
+        part[(size_t)(pair0 + pl) * M + k] = t;
+    }
 }
 
 // grad[m] = scale * sum over pairs of part[k = m] + part[k = M - m] (m = 1..M/2-1), fixed order;
@@ -347,7 +374,7 @@ static AdjLayout adj_layout(const bst_plan_s* p, int pairs, void* ws) {
 
 template <int M>
 static bst_status_t adjoint_chunk(bst_plan_s* p, const AdjLayout& L, const float* vol, int slices, int p0, int np,
-                                  int mode, const float* g, float* sino, cudaStream_t st) {
+                                  int mode, const float* g, float* sino, bool keep_lam, cudaStream_t st) {
     using C = AdjCfg<M>;
     static bool attr = set_smem_a(k_adj_row_fft<M, C::TPL, C::TPC>, C::S1) &&
                        set_smem_a(k_adj_col_fft<M, C::TPL, C::LPC>, C::S2) &&
@@ -365,7 +392,7 @@ static bst_status_t adjoint_chunk(bst_plan_s* p, const AdjLayout& L, const float
     Cells cl{p->cell_start, p->cell_pts, p->cell_w};
     const float scale = (float)((double)N / (2.0 * (double)M * (double)M));
     k_adj_polar<M, C::TPL, C::LPC><<<dim3((V + C::LPC - 1) / C::LPC, np), C::TPL * C::LPC, C::S2, st>>>(
-        L.X, cl, V, N, slices, p0, mode, g, (float)(2 * p->alpha), scale, sino, L.lam, p->tw);
+        L.X, cl, V, N, slices, p0, mode, g, (float)(2 * p->alpha), scale, sino, keep_lam ? L.lam : nullptr, p->tw);
     bst_timing_mark(p, st, 7);
     return BST_OK;
 }
@@ -429,10 +456,11 @@ bst_status_t bst_build_cells(bst_plan_s* p, cudaStream_t st) {
 }
 
 static bst_status_t adjoint_chunk_dispatch(bst_plan_s* p, const bst::AdjLayout& L, const float* vol, int slices,
-                                           int p0, int np, int mode, const float* g, float* sino, cudaStream_t st) {
+                                           int p0, int np, int mode, const float* g, float* sino, bool keep_lam,
+                                           cudaStream_t st) {
     switch (p->M) {
 #define BST_CASE(m) \
-    case m: return bst::adjoint_chunk<m>(p, L, vol, slices, p0, np, mode, g, sino, st);
+    case m: return bst::adjoint_chunk<m>(p, L, vol, slices, p0, np, mode, g, sino, keep_lam, st);
         BST_FOR_EACH_M(BST_CASE)
 #undef BST_CASE
     }
@@ -447,7 +475,7 @@ bst_status_t bst_launch_adjoint(bst_plan_s* p, int mode, const float* g, const f
     const bst::AdjLayout L = bst::adj_layout(p, pairs, ws);
     for (int p0 = 0; p0 < pairs; p0 += L.chunk) {
         const int np = std::min(L.chunk, pairs - p0);
-        s = adjoint_chunk_dispatch(p, L, vol, slices, p0, np, mode, g, sino, st);
+        s = adjoint_chunk_dispatch(p, L, vol, slices, p0, np, mode, g, sino, false, st);
         if (s != BST_OK) return s;
     }
     return cudaGetLastError() == cudaSuccess ? BST_OK : BST_ERR_CUDA;
@@ -457,8 +485,11 @@ bst_status_t bst_launch_adjoint(bst_plan_s* p, int mode, const float* g, const f
 bst_status_t bst_launch_ray_spectrum(bst_plan_s* p, const float* sino, int slices, int p0, int np, float2* Y,
                                      cudaStream_t st);
 
-bst_status_t bst_launch_filter_grad(bst_plan_s* p, const float* sino, const float* gvol, int slices, float* grad_g,
-                                    void* ws, size_t /*ws_bytes*/, cudaStream_t st) {
+// Both gradients of <grad_vol, FBP(sino; g)>: grad_sino = the adjoint applied to
+// grad_vol (taps g; skipped when null), grad_g = sum Re(conj(lambda) Y) (skipped
+// when null), from one pull-back lambda per chunk.
+bst_status_t bst_launch_backward(bst_plan_s* p, const float* sino, const float* gvol, int slices, const float* g,
+                                 float* grad_sino, float* grad_g, void* ws, cudaStream_t st) {
     bst_status_t s = bst_build_cells(p, st);
     if (s != BST_OK) return s;
     const int pairs = (slices + 1) / 2;
@@ -466,13 +497,24 @@ bst_status_t bst_launch_filter_grad(bst_plan_s* p, const float* sino, const floa
     const int M = p->M, V = p->V;
     for (int p0 = 0; p0 < pairs; p0 += L.chunk) {
         const int np = std::min(L.chunk, pairs - p0);
-        s = adjoint_chunk_dispatch(p, L, gvol, slices, p0, np, BSTK_RAW, nullptr, nullptr, st);
+        s = adjoint_chunk_dispatch(p, L, gvol, slices, p0, np, grad_sino ? BSTK_FILTER : BSTK_RAW, g, grad_sino,
+                                   grad_g != nullptr, st);
         if (s != BST_OK) return s;
-        s = bst_launch_ray_spectrum(p, sino, slices, p0, np, L.Y, st);
-        if (s != BST_OK) return s;
-        bst::k_fg_partial<<<dim3((M + 255) / 256, np), 256, 0, st>>>(L.lam, L.Y, V, M, p0, L.part);
+        if (grad_g) {
+            s = bst_launch_ray_spectrum(p, sino, slices, p0, np, L.Y, st);
+            if (s != BST_OK) return s;
+            bst::k_fg_partial<<<dim3((M + bst::FG_K - 1) / bst::FG_K, np), bst::FG_K * bst::FG_G, 0, st>>>(
+                L.lam, L.Y, V, M, p0, L.part);
+        }
     }
-    const float scale = (float)((double)p->N / (2.0 * (double)M * (double)M));
-    bst::k_fg_final<<<(M / 2 + 255) / 256, 256, 0, st>>>(L.part, pairs, M, scale, grad_g);
+    if (grad_g) {
+        const float scale = (float)((double)p->N / (2.0 * (double)M * (double)M));
+        bst::k_fg_final<<<(M / 2 + 255) / 256, 256, 0, st>>>(L.part, pairs, M, scale, grad_g);
+    }
     return cudaGetLastError() == cudaSuccess ? BST_OK : BST_ERR_CUDA;
+}
+
+bst_status_t bst_launch_filter_grad(bst_plan_s* p, const float* sino, const float* gvol, int slices, float* grad_g,
+                                    void* ws, size_t /*ws_bytes*/, cudaStream_t st) {
+    return bst_launch_backward(p, sino, gvol, slices, nullptr, nullptr, grad_g, ws, st);
 }

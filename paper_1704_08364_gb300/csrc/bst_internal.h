@@ -133,6 +133,8 @@ bst_status_t bst_launch_adjoint(bst_plan_s* p, int mode, const float* g, const f
                                 float* sino, void* ws, size_t ws_bytes, cudaStream_t st);
 bst_status_t bst_launch_filter_grad(bst_plan_s* p, const float* sino, const float* gvol, int slices,
                                     float* grad_g, void* ws, size_t ws_bytes, cudaStream_t st);
+bst_status_t bst_launch_backward(bst_plan_s* p, const float* sino, const float* gvol, int slices, const float* g,
+                                 float* grad_sino, float* grad_g, void* ws, cudaStream_t st);
 bst_status_t bst_launch_brute(bst_plan_s* p, const float* sino, int slices, const float* g, float* vol,
                               void* ws, size_t ws_bytes, cudaStream_t st);
 bst_status_t bst_build_cells(bst_plan_s* p, cudaStream_t st);

@@ -304,6 +304,18 @@ bst_status_t bst_fbp_filter_grad(bst_plan_t p, const float* d_sino, const float*
     return bst_launch_filter_grad(p, d_sino, d_grad_vol, slices, d_grad_g, d_ws, ws_bytes, (cudaStream_t)stream);
 }
 
+bst_status_t bst_fbp_backward(bst_plan_t p, const float* d_sino, const float* d_grad_vol, int slices,
+                              const float* d_g, float* d_grad_sino, float* d_grad_g, void* d_ws, size_t ws_bytes,
+                              bst_stream_t stream) {
+    if (!p || !d_grad_vol || slices <= 0 || (!d_grad_sino && !d_grad_g)) return BST_ERR_INVALID_ARGUMENT;
+    if (d_grad_g && !d_sino) return BST_ERR_INVALID_ARGUMENT;
+    if (p->grid_kind != BST_GRID_BILINEAR) return BST_ERR_INVALID_ARGUMENT;
+    const size_t nv = (size_t)slices * p->N * p->N * sizeof(float), ns = (size_t)slices * p->V * p->N * sizeof(float);
+    if (d_grad_sino && ranges_overlap(d_grad_sino, ns, d_grad_vol, nv)) return BST_ERR_INVALID_ARGUMENT;
+    if (!d_ws || ws_bytes < bst_adjoint_ws(p, slices)) return BST_ERR_WORKSPACE_TOO_SMALL;
+    return bst_launch_backward(p, d_sino, d_grad_vol, slices, d_g, d_grad_sino, d_grad_g, d_ws, (cudaStream_t)stream);
+}
+
 bst_status_t brute_backproject(bst_plan_t p, const float* d_sino, int slices, const float* d_g, float* d_volume,
                                void* d_ws, size_t ws_bytes, bst_stream_t stream) {
     bst_status_t s = check_io(p, d_sino, slices, d_volume);

@@ -58,5 +58,6 @@ def test_invalid_arguments_need_no_device(lib):
     assert L.bst_fbp(None, None, 1, None, None, None, 0, None) == 1
     assert L.bst_workspace_bytes(None, 4) == 0
     assert L.bst_plan_set_gridding(None, 1, 6) == 1
+    assert L.bst_fbp_backward(None, None, None, 1, None, None, None, None, 0, None) == 1
     k, w = ctypes.c_int(0), ctypes.c_int(0)
     assert L.bst_plan_get_gridding(None, ctypes.byref(k), ctypes.byref(w)) == 1

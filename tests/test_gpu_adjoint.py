@@ -83,3 +83,26 @@ def test_autograd_function(bst):
     gg_ref = sum(oa.filter_grad(p[s].astype(np.float64), R[s], theta) for s in range(2))
     assert_parity(dp.grad.cpu().numpy(), gp_ref, what="grad p")
     assert_parity(g.grad.cpu().numpy(), gg_ref, what="grad g")
+
+
+def test_backward_equals_the_two_separate_calls(bst):
+    """bst_fbp_backward (one pull-back for both gradients) gives what
+    radon_adjoint and bst_fbp_filter_grad give separately, with either output
+    alone too; odd slice count, random taps."""
+    rng = np.random.default_rng(12)
+    N, V, S = 128, 96, 3
+    theta = synth.uniform_angles(V)
+    plan = bst.Plan(N, theta, 2)
+    p = _cuda(rng.standard_normal((S, V, N)))
+    R = _cuda(rng.standard_normal((S, N, N)))
+    g = _cuda(rng.uniform(0.5, 1.5, N))
+    gp, gg = plan.fbp_backward(p, R, g)
+    ref_p = plan.radon_adjoint(R, bst.FILTER, g)
+    ref_g = plan.filter_grad(p, R)
+    assert_parity(gp.cpu().numpy(), ref_p.cpu().numpy(), rtol_l2=1e-7, atol_frac=1e-6, what="backward grad p")
+    assert_parity(gg.cpu().numpy(), ref_g.cpu().numpy(), rtol_l2=1e-7, atol_frac=1e-6, what="backward grad g")
+    only_p, none_g = plan.fbp_backward(p, R, g, want_g=False)
+    none_p, only_g = plan.fbp_backward(p, R, g, want_sino=False)
+    assert none_g is None and none_p is None
+    assert_parity(only_p.cpu().numpy(), ref_p.cpu().numpy(), rtol_l2=1e-7, atol_frac=1e-6, what="grad p alone")
+    assert_parity(only_g.cpu().numpy(), ref_g.cpu().numpy(), rtol_l2=1e-7, atol_frac=1e-6, what="grad g alone")
