@@ -82,9 +82,9 @@ STAGE_NAMES = {0: "k_ray_fft", 1: "k_grid_col", 2: "k_row_ifft", 3: "k_ss_filter
 KERNEL_SOURCES = ["paper_1704_08364_gb300/csrc/bst_forward.cuh", "paper_1704_08364_gb300/csrc/bst_stages.cuh",
                   "paper_1704_08364_gb300/csrc/bst_fft.cuh", "paper_1704_08364_gb300/csrc/bst_geo.cuh"]
 CAPTURED_TRAFFIC = {
-    "sha": "09a3c27da34b0bc49e3230fe240ddc4e098d7c19a866625c8eba004fe734f717",
+    "sha": "0858670ed8296075e48aeed211af5661946faf8f209bc2104bab9f9ecad6ca62",
     "rays": 2048, "pad": 2,
-    "bytes": {"k_ray_fft": 33609472 + 9562880, "k_grid_col": 167624192 + 39220736, "k_row_ifft": 67151360 + 4377088},
+    "bytes": {"k_ray_fft": 33608960 + 9567488, "k_grid_col": 167623424 + 39298816, "k_row_ifft": 67157504 + 5480704},
 }
 
 
