@@ -361,7 +361,9 @@ def run_ours(args, rank, world):
     # host<->device link of this machine is shared with other jobs, so the
     # fastest and slowest step are reported beside the mean.
     e2e = None
-    es = min(args.e2e_slices, S)
+    # one 2048-slice volume of pinned host memory per node: with N ranks each
+    # rank streams its 1/N share of it
+    es = min(args.e2e_slices, S, max(2, (2048 // world) & ~1))
     try:
         h_in = torch.empty((es, V, N), dtype=torch.float32, pin_memory=True)
         h_in.copy_(sino[:es])
@@ -441,7 +443,7 @@ def run_ours(args, rank, world):
     # the ragged batch: 64 sinograms of mixed sizes, one persistent launch
     # (direct and replayed from a CUDA graph) vs plain per-size launches
     ragged = autograd = pad1 = kbg = None
-    if not args.no_extras:
+    if not args.no_extras and world == 1:
         pad1 = bench_pad1(bst, theta, sino, vol, args.steps, hbm_peak)
         kbg = bench_kb(bst, theta, sino, vol, args.steps)
         ragged = bench_ragged(bst, synth, sdev, dev, args.steps)
