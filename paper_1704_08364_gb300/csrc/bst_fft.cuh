@@ -345,6 +345,51 @@ __device__ __forceinline__ void fft_line(int t, const Src& src, const Dst& dst, 
     fft_run<M, TPL, INV, MAXR, 0, 1>(t, src, dst, sm, tw);
 }
 
+// The transform of a line whose values thread t already holds in registers,
+// x[i] = line[t + i TPL] for i < M / TPL (the order in which a gather fills the
+// line).  These are exactly the first pass's inputs of butterflies
+// j = t + it TPL: element j + s M/R is x[it + s IT].  So pass 0 runs on them
+// directly and only its outputs go to the shared-memory line `sm`; the later
+// passes are those of fft_line.  Call with every thread of the block; `sm`
+// must be free for writing (the caller's barrier).
+template <int M, int TPL, bool INV, int MAXR = 16, class Dst>
+__device__ __forceinline__ void fft_line_regs(int t, float2 (&x)[M / TPL], const Dst& dst, const SmemLine& sm,
+                                              const float2* __restrict__ tw) {
+    constexpr int R = radix_of(M, 0, MAXR);
+    constexpr int NB = M / R;
+    static_assert(NB % TPL == 0, "one or more whole first-pass butterflies per thread");
+    constexpr int IT = NB / TPL;
+    if constexpr (R == M) {
+        // a single pass: one thread holds the whole line
+        Dft<R, INV>::run(x);
+#pragma unroll
+        for (int s = 0; s < R; ++s)
+            if (!dst_drop_group<Dst, M>(s, s + 1)) dst.store(s, x[s]);
+        return;
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        float2 a[R];
+#pragma unroll
+        for (int s = 0; s < R; ++s) a[s] = x[it + s * IT];
+        Dft<R, INV>::run(a);
+        const int base = (t + it * TPL) * R;
+        if constexpr (16 % R == 0) {
+            // base is a multiple of R, so the R outputs stay in one 16-group
+            float2* p = sm.p + base + (base >> 4);
+#pragma unroll
+            for (int s = 0; s < R; ++s) p[s] = a[s];
+        } else {
+#pragma unroll
+            for (int s = 0; s < R; ++s) sm.store(base + s, a[s]);
+        }
+    }
+    if constexpr (R < M) {
+        __syncthreads();
+        fft_run<M, TPL, INV, MAXR, 1, R>(t, sm, dst, sm, tw);
+    }
+}
+
 // signed frequency of natural-order index p
 __device__ __forceinline__ int signed_freq(int p, int M) { return p < (M >> 1) ? p : p - M; }
 

@@ -96,11 +96,12 @@ struct ColDst {
 
 // Bilinear gather of one side of a column pair: plus = true for the point
 // (q, r') itself (kappa = +rho when P.up), false for its mirror (-q, -r').
-// Two points per step; all eight tap loads are issued before any is used.
+// Thread t gathers rows t + i TPL into x[i], the first FFT pass's inputs.  Two
+// points per step; all eight tap loads are issued before any is used.
 template <int M, int TPL, int PPT>
 __device__ __forceinline__ void gather_side(const float2* __restrict__ Zp, int V, int q, bool live, int t,
                                             const int* __restrict__ gJq, const float2* __restrict__ gFq,
-                                            bool mirror, const SmemLine& sm) {
+                                            bool mirror, float2 (&x)[PPT]) {
     constexpr int H = M >> 1;
     const float2 zero = make_float2(0.f, 0.f);
     // the plan's table (bracket and floor(rho) packed; angle and radius
@@ -113,7 +114,7 @@ __device__ __forceinline__ void gather_side(const float2* __restrict__ Zp, int V
         jn[u] = __ldg(gJq + t + (u < PPT ? u : 0) * TPL);
         fn[u] = __ldg(gFq + t + (u < PPT ? u : 0) * TPL);
     }
-#pragma unroll 1
+#pragma unroll
     for (int i = 0; i < PPT; i += 2) {
         float2 z[2][4];
         float wk[2], wt[2];
@@ -196,7 +197,7 @@ __device__ __forceinline__ void gather_side(const float2* __restrict__ Zp, int V
             const float2 z00 = z[u][0], z01 = z[u][1], z10 = z[u][2], z11 = z[u][3];
             const float2 a = make_float2(fmaf(fk, z01.x - z00.x, z00.x), fmaf(fk, z01.y - z00.y, z00.y));
             const float2 b = make_float2(fmaf(fk, z11.x - z10.x, z10.x), fmaf(fk, z11.y - z10.y, z10.y));
-            sm.store(t + (i + u) * TPL, make_float2(fmaf(ft, b.x - a.x, a.x), fmaf(ft, b.y - a.y, a.y)));
+            x[i + u] = make_float2(fmaf(ft, b.x - a.x, a.x), fmaf(ft, b.y - a.y, a.y));
         }
     }
 }
@@ -379,12 +380,15 @@ __device__ __forceinline__ void grid_unit(float2* smem, int q0, int V, int N, co
     const float2* gFq = gF + (size_t)(live ? q : 0) * M;
 #pragma unroll 1
     for (int side = 0; side < 2; ++side) {
+        float2 x[PPT];
         if (side == 0 || q != 0) {
-            gather_side<M, TPL, PPT>(Zp, V, q, live, t, gJq, gFq, side == 1, sm);
+            gather_side<M, TPL, PPT>(Zp, V, q, live, t, gJq, gFq, side == 1, x);
         } else {
-            for (int i = 0; i < PPT; ++i) sm.store(t + i * TPL, make_float2(0.f, 0.f));
+#pragma unroll
+            for (int i = 0; i < PPT; ++i) x[i] = make_float2(0.f, 0.f);
         }
-        // the origin is single-valued: mean over angles of the DC bin
+        // the origin is single-valued: mean over angles of the DC bin (row 0 of
+        // thread 0's rows)
         if (side == 0 && live && q == 0) {
             if constexpr (TPL >= 32) {
                 if (t < 32) {
@@ -399,7 +403,7 @@ __device__ __forceinline__ void grid_unit(float2* smem, int q0, int V, int N, co
                         sx += __shfl_xor_sync(0xffffffffu, sx, o);
                         sy += __shfl_xor_sync(0xffffffffu, sy, o);
                     }
-                    if (t == 0) sm.store(0, make_float2(sx / (float)V, sy / (float)V));
+                    if (t == 0) x[0] = make_float2(sx / (float)V, sy / (float)V);
                 }
             } else {
                 if (t == 0) {
@@ -409,14 +413,14 @@ __device__ __forceinline__ void grid_unit(float2* smem, int q0, int V, int N, co
                         sx += zz.x;
                         sy += zz.y;
                     }
-                    sm.store(0, make_float2(sx / (float)V, sy / (float)V));
+                    x[0] = make_float2(sx / (float)V, sy / (float)V);
                 }
             }
         }
-        __syncthreads();
+        // side 0's last pass may still read the line
+        if (side == 1) __syncthreads();
         const ColDst<NC> dst{Tp, N, M, side == 0 ? q : (q == 0 ? (M >> 1) : M - q), side == 1 && q != 0, live};
-        fft_line<M, TPL, true, MAXR>(t, sm, dst, sm, tw);
-        __syncthreads();
+        fft_line_regs<M, TPL, true, MAXR>(t, x, dst, sm, tw);
     }
 }
 
