@@ -96,43 +96,47 @@ struct ColDst {
 
 // Bilinear gather of one side of a column pair: plus = true for the point
 // (q, r') itself (kappa = +rho when P.up), false for its mirror (-q, -r').
-// Thread t gathers rows t + i TPL into x[i], the first FFT pass's inputs.  Two
-// points per step; all eight tap loads are issued before any is used.
-template <int M, int TPL, int PPT>
+// Thread t gathers rows t + i TPL into x[i], the first FFT pass's inputs.  PS
+// points per step; all 4 PS tap loads of a step are issued before any is used.
+template <int M, int TPL, int PPT, int PS = 2>
 __device__ __forceinline__ void gather_side(const float2* __restrict__ Zp, int V, int q, bool live, int t,
                                             const int* __restrict__ gJq, const float2* __restrict__ gFq,
                                             bool mirror, float2 (&x)[PPT]) {
+    static_assert(PPT % PS == 0, "points per step");
     constexpr int H = M >> 1;
     const float2 zero = make_float2(0.f, 0.f);
     // the plan's table (bracket and floor(rho) packed; angle and radius
     // fractions), prefetched two steps ahead so that each step waits on the
     // tap loads only
-    int jn[4];
-    float2 fn[4];
+    int jn[2 * PS];
+    float2 fn[2 * PS];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 2 * PS; ++u) {
         jn[u] = __ldg(gJq + t + (u < PPT ? u : 0) * TPL);
         fn[u] = __ldg(gFq + t + (u < PPT ? u : 0) * TPL);
     }
 #pragma unroll
-    for (int i = 0; i < PPT; i += 2) {
-        float2 z[2][4];
-        float wk[2], wt[2];
-        const int jc[2] = {jn[0], jn[1]};
-        const float2 fc[2] = {fn[0], fn[1]};
-        jn[0] = jn[2];
-        jn[1] = jn[3];
-        fn[0] = fn[2];
-        fn[1] = fn[3];
-        if (i + 4 < PPT) {
+    for (int i = 0; i < PPT; i += PS) {
+        float2 z[PS][4];
+        float wk[PS], wt[PS];
+        int jc[PS];
+        float2 fc[PS];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                jn[2 + u] = __ldg(gJq + t + (i + 4 + u) * TPL);
-                fn[2 + u] = __ldg(gFq + t + (i + 4 + u) * TPL);
+        for (int u = 0; u < PS; ++u) {
+            jc[u] = jn[u];
+            fc[u] = fn[u];
+            jn[u] = jn[PS + u];
+            fn[u] = fn[PS + u];
+        }
+        if (i + 2 * PS < PPT) {
+#pragma unroll
+            for (int u = 0; u < PS; ++u) {
+                jn[PS + u] = __ldg(gJq + t + (i + 2 * PS + u) * TPL);
+                fn[PS + u] = __ldg(gFq + t + (i + 2 * PS + u) * TPL);
             }
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < PS; ++u) {
             const int ridx = t + (i + u) * TPL;
             const int ry = signed_freq(ridx, M);
             const int jk = jc[u];
@@ -184,15 +188,15 @@ __device__ __forceinline__ void gather_side(const float2* __restrict__ Zp, int V
                 o10 = v10 ? rowB * M + (b10 < 0 ? b10 + M : b10) : 0;
                 o11 = v11 ? rowB * M + (b11 < 0 ? b11 + M : b11) : 0;
             }
-            const float2 a00 = __ldg(Zp + o00), a01 = __ldg(Zp + o01);
-            const float2 a10 = __ldg(Zp + o10), a11 = __ldg(Zp + o11);
-            z[u][0] = v00 ? a00 : zero;
-            z[u][1] = v01 ? a01 : zero;
-            z[u][2] = v10 ? a10 : zero;
-            z[u][3] = v11 ? a11 : zero;
+            // taps outside the band (about a fifth of the grid's points lie
+            // beyond rho = M/2, mostly in whole warps) issue no load
+            z[u][0] = v00 ? __ldg(Zp + o00) : zero;
+            z[u][1] = v01 ? __ldg(Zp + o01) : zero;
+            z[u][2] = v10 ? __ldg(Zp + o10) : zero;
+            z[u][3] = v11 ? __ldg(Zp + o11) : zero;
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
+        for (int u = 0; u < PS; ++u) {
             const float fk = wk[u], ft = wt[u];
             const float2 z00 = z[u][0], z01 = z[u][1], z10 = z[u][2], z11 = z[u][3];
             const float2 a = make_float2(fmaf(fk, z01.x - z00.x, z00.x), fmaf(fk, z01.y - z00.y, z00.y));
