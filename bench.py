@@ -82,9 +82,9 @@ STAGE_NAMES = {0: "k_ray_fft", 1: "k_grid_col", 2: "k_row_ifft", 3: "k_ss_filter
 KERNEL_SOURCES = ["paper_1704_08364_gb300/csrc/bst_forward.cuh", "paper_1704_08364_gb300/csrc/bst_stages.cuh",
                   "paper_1704_08364_gb300/csrc/bst_fft.cuh", "paper_1704_08364_gb300/csrc/bst_geo.cuh"]
 CAPTURED_TRAFFIC = {
-    "sha": "0858670ed8296075e48aeed211af5661946faf8f209bc2104bab9f9ecad6ca62",
+    "sha": "d51f783999096b0d484d060755b23678517f80beed765cf59aa1ef3e9f5f0593",
     "rays": 2048, "pad": 2,
-    "bytes": {"k_ray_fft": 33608960 + 9567488, "k_grid_col": 167623424 + 39298816, "k_row_ifft": 67157504 + 5480704},
+    "bytes": {"k_ray_fft": 33603328 + 9010688, "k_grid_col": 167751424 + 39462912, "k_row_ifft": 67147008 + 4858368},
 }
 
 
