@@ -107,7 +107,7 @@ static bool upload_vec(T** d, const std::vector<T>& h) {
 //   by the first row of its footprint (r' - r_s > -W/2, taken mod M);
 //   per band of four rows of the strip, the range of that list whose footprint
 //   meets the band (two ranges at the wrap), cut into work items of at most
-//   KB_ITEM entries.
+//   KB_ITEM entries; a strip's items ordered longest first.
 static bst_status_t build_kb(bst_plan_s* p, int W) {
     using bst::KB_CS;
     using bst::KB_ITEM;
@@ -206,6 +206,10 @@ static bst_status_t build_kb(bst_plan_s* p, int W) {
                 emit(b, row_pos(s, 0), row_pos(s, hi));
             }
         }
+        // longest first: the lanes of a warp then take items of about the same
+        // length, and the block's last round of items is its shortest
+        std::stable_sort(items.begin() + istart[s], items.end(),
+                         [](const int4& a, const int4& b) { return a.z - a.y > b.z - b.y; });
         istart[s + 1] = (int)items.size();
     }
 
