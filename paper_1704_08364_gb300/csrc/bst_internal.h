@@ -87,6 +87,9 @@ namespace bsth {
 // chunks of the forward path in flight at once, each on its own stream with its
 // own workspace (a third one measured no faster than two at 2048^3)
 constexpr int kMaxLanes = 2;
+static_assert(kMaxLanes <= (int)(sizeof(bst_plan_s::lane) / sizeof(cudaStream_t)) &&
+                  kMaxLanes <= (int)(sizeof(bst_plan_s::ev_join) / sizeof(cudaEvent_t)),
+              "the plan holds a stream and a join event per lane");
 
 inline bool supported_fft_length(int M) {
     int m = M;
