@@ -376,10 +376,13 @@ template <int M>
 static bst_status_t adjoint_chunk(bst_plan_s* p, const AdjLayout& L, const float* vol, int slices, int p0, int np,
                                   int mode, const float* g, float* sino, bool keep_lam, cudaStream_t st) {
     using C = AdjCfg<M>;
-    static bool attr = set_smem_a(k_adj_row_fft<M, C::TPL, C::TPC>, C::S1) &&
-                       set_smem_a(k_adj_col_fft<M, C::TPL, C::LPC>, C::S2) &&
-                       set_smem_a(k_adj_polar<M, C::TPL, C::LPC>, C::S2);
-    if (!attr) return BST_ERR_CUDA;
+    static std::atomic<unsigned long long> attr_done{0};
+    if (!bsth::once_per_device(attr_done, [] {
+            return set_smem_a(k_adj_row_fft<M, C::TPL, C::TPC>, C::S1) &&
+                   set_smem_a(k_adj_col_fft<M, C::TPL, C::LPC>, C::S2) &&
+                   set_smem_a(k_adj_polar<M, C::TPL, C::LPC>, C::S2);
+        }))
+        return BST_ERR_CUDA;
     const int N = p->N, V = p->V;
     const int row_tiles = (N + 3) / 4;
     bst_timing_mark(p, st, -1);

@@ -170,10 +170,13 @@ bst_status_t launch_ss_filter_M(bst_plan_s* p, const float* sino, int slices, co
     constexpr int TPL = brute_tpl<M>();
     constexpr int LPC = (256 / TPL) > 1 ? 256 / TPL : 1;
     constexpr size_t S = (size_t)LPC * smem_line_len(M) * sizeof(float2);
-    static bool attr = S <= 48 * 1024 ||
-                       cudaFuncSetAttribute(k_ss_filter<M, TPL, LPC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)S) == cudaSuccess;
-    if (!attr) return BST_ERR_CUDA;
+    static std::atomic<unsigned long long> attr_done{0};
+    if (!bsth::once_per_device(attr_done, [] {
+            return S <= 48 * 1024 || cudaFuncSetAttribute(k_ss_filter<M, TPL, LPC>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)S) == cudaSuccess;
+        }))
+        return BST_ERR_CUDA;
     const int pairs = (slices + 1) / 2;
     const float dsig = (float)((double)p->N / (2.0 * (double)M));
     bst_timing_mark(p, st, -1);

@@ -109,11 +109,14 @@ template <int M, int MAXR, int NC>
 bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int mode, const float* g, float* vol,
                               void* ws, cudaStream_t st, int max_chunk, int lanes, const PrepArgs* prep) {
     using C = FwdCfg<M>;
-    static bool attr_ok = set_smem(k_ray_fft<M, C::TPL, C::LPC1, MAXR, NC>, C::S1) &&
-                          set_smem(k_ray_fft_prep<M, C::TPL, C::LPC1, MAXR, NC>, C::S1) &&
-                          set_smem(k_grid_col<M, C::TPL, C::CPC, MAXR, NC>, C::S2) &&
-                          set_smem(k_row_ifft<M, C::TPL, C::TPC, MAXR, NC>, C::S3);
-    if (!attr_ok) return BST_ERR_CUDA;
+    static std::atomic<unsigned long long> attr_done{0};
+    if (!bsth::once_per_device(attr_done, [] {
+            return set_smem(k_ray_fft<M, C::TPL, C::LPC1, MAXR, NC>, C::S1) &&
+                   set_smem(k_ray_fft_prep<M, C::TPL, C::LPC1, MAXR, NC>, C::S1) &&
+                   set_smem(k_grid_col<M, C::TPL, C::CPC, MAXR, NC>, C::S2) &&
+                   set_smem(k_row_ifft<M, C::TPL, C::TPC, MAXR, NC>, C::S3);
+        }))
+        return BST_ERR_CUDA;
     const int N = p->N, V = p->V;
     const int pairs = (slices + 1) / 2;
     const int chunk = std::min(pairs, max_chunk);

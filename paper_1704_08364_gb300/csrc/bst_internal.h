@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <vector>
 
 #include "../../include/bst.h"
@@ -90,6 +92,22 @@ constexpr int kMaxLanes = 2;
 static_assert(kMaxLanes <= (int)(sizeof(bst_plan_s::lane) / sizeof(cudaStream_t)) &&
                   kMaxLanes <= (int)(sizeof(bst_plan_s::ev_join) / sizeof(cudaEvent_t)),
               "the plan holds a stream and a join event per lane");
+
+// The opt-in to more than 48 KB of dynamic shared memory is an attribute of a
+// kernel on one device.  A launch site keeps one bit per device in `done` and
+// runs `set` (which sets its kernels' attributes on the current device) the
+// first time it launches on that device; on devices beyond 63 it runs `set`
+// every time.
+template <class F>
+inline bool once_per_device(std::atomic<unsigned long long>& done, F&& set) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return true;
+    if (!set()) return false;
+    if (bit) done.fetch_or(bit, std::memory_order_release);
+    return true;
+}
 
 inline bool supported_fft_length(int M) {
     int m = M;

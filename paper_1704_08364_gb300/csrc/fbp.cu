@@ -70,8 +70,9 @@ template <int M>
 bst_status_t launch_ray_spectrum_M(bst_plan_s* p, const float* sino, int slices, int p0, int np, float2* Y,
                                    cudaStream_t st) {
     using C = FwdCfg<M>;
-    static bool attr_ok = set_smem(k_ray_fft<M, C::TPL, C::LPC1, 16, 0>, C::S1);
-    if (!attr_ok) return BST_ERR_CUDA;
+    static std::atomic<unsigned long long> attr_done{0};
+    if (!bsth::once_per_device(attr_done, [] { return set_smem(k_ray_fft<M, C::TPL, C::LPC1, 16, 0>, C::S1); }))
+        return BST_ERR_CUDA;
     bst_timing_mark(p, st, -1);
     k_ray_fft<M, C::TPL, C::LPC1, 16, 0><<<dim3((p->V + C::LPC1 - 1) / C::LPC1, np), C::TPL * C::LPC1, C::S1, st>>>(
         sino, slices, p0, p->N, p->V, BSTK_RAW, nullptr, 0.f, Y, p->tw);

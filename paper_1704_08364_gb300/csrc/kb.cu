@@ -36,9 +36,12 @@ __global__ void __launch_bounds__(kb_threads<M>(), 1)
 template <int M, int MAXR>
 bst_status_t launch_kb_col_M(bst_plan_s* p, const float2* Z, float2* T, int np, cudaStream_t st) {
     constexpr size_t smem = kb_smem_bytes<M>();
-    static const bool attr_ok =
-        cudaFuncSetAttribute(k_kb_col<M, MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
-    if (!attr_ok) return BST_ERR_CUDA;
+    static std::atomic<unsigned long long> attr_done{0};
+    if (!bsth::once_per_device(attr_done, [] {
+            return cudaFuncSetAttribute(k_kb_col<M, MAXR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                   cudaSuccess;
+        }))
+        return BST_ERR_CUDA;
     KbArgs a;
     a.tab = p->kb_tab;
     a.istart = p->kb_start;
