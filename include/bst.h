@@ -29,6 +29,12 @@
  * covers argument validation and launch errors only; errors detected on the
  * device are sticky in the plan and reported by bst_plan_status().  Calls on
  * one plan may be issued from one host thread at a time.
+ *
+ * A plan belongs to the device that was current at bst_plan_create (its
+ * tables live there).  Every call that launches work for a plan or builds
+ * tables for it must be made with that device current, and returns
+ * BST_ERR_INVALID_ARGUMENT otherwise; so do the ragged-batch calls, whose
+ * plans must all belong to the current device.
  */
 #ifndef BST_H
 #define BST_H

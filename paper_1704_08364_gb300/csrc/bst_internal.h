@@ -93,6 +93,13 @@ static_assert(kMaxLanes <= (int)(sizeof(bst_plan_s::lane) / sizeof(cudaStream_t)
                   kMaxLanes <= (int)(sizeof(bst_plan_s::ev_join) / sizeof(cudaEvent_t)),
               "the plan holds a stream and a join event per lane");
 
+// A plan's tables live on the device that was current at its creation; the
+// calls that launch work or build tables for it check that it is current.
+inline bool on_plan_device(const bst_plan_s* p) {
+    int dev = -1;
+    return cudaGetDevice(&dev) == cudaSuccess && dev == p->device;
+}
+
 // The opt-in to more than 48 KB of dynamic shared memory is an attribute of a
 // kernel on one device.  A launch site keeps one bit per device in `done` and
 // runs `set` (which sets its kernels' attributes on the current device) the

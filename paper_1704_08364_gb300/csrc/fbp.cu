@@ -107,6 +107,7 @@ extern "C" bst_status_t bst_fbp_prep(bst_plan_t p, const float* d_sino, int slic
                                      const float* d_g, float* d_volume, void* d_ws, size_t ws_bytes,
                                      bst_stream_t stream) {
     if (!p || !d_sino || !d_volume || slices <= 0) return BST_ERR_INVALID_ARGUMENT;
+    if (!bsth::on_plan_device(p)) return BST_ERR_INVALID_ARGUMENT;
     if (d_dark && !d_flat) return BST_ERR_INVALID_ARGUMENT;
     if (!std::isfinite(shift) || std::fabs(shift) >= (float)p->N) return BST_ERR_INVALID_ARGUMENT;
     if (!(kb_beta >= 0.f) || !std::isfinite(kb_beta) || (kb_beta > 0.f && !(kb_halfwidth > 0.f)))

@@ -50,6 +50,7 @@ size_t bst_host_workspace_bytes(bst_plan_t p, int slices) {
 bst_status_t bst_fbp_host(bst_plan_t p, const float* h_sino, int slices, const float* d_g, float* h_volume,
                           void* d_ws, size_t ws_bytes, bst_stream_t stream) {
     if (!p || !h_sino || !h_volume || slices <= 0) return BST_ERR_INVALID_ARGUMENT;
+    if (!bsth::on_plan_device(p)) return BST_ERR_INVALID_ARGUMENT;
     if (!d_ws || ws_bytes < bst_host_workspace_bytes(p, slices)) return BST_ERR_WORKSPACE_TOO_SMALL;
     if (!ensure_host_streams(p)) return BST_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;

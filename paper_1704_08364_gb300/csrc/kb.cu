@@ -234,6 +234,7 @@ extern "C" {
 
 bst_status_t bst_plan_set_gridding(bst_plan_t p, int kind, int width) {
     if (!p) return BST_ERR_INVALID_ARGUMENT;
+    if (!bsth::on_plan_device(p)) return BST_ERR_INVALID_ARGUMENT;
     if (kind == BST_GRID_BILINEAR) {
         cudaDeviceSynchronize();
         bst_free_kb(p);

@@ -61,6 +61,7 @@ size_t bst_noalloc_scratch_bytes(void) { return BST_NOALLOC_SCRATCH_BYTES; }
 bst_status_t bst_fbp_noalloc(bst_plan_t p, const float* d_sino, int slices, const float* d_g, float* d_volume,
                              bst_stream_t stream) {
     if (!p || !d_sino || !d_volume || slices <= 0) return BST_ERR_INVALID_ARGUMENT;
+    if (!bsth::on_plan_device(p)) return BST_ERR_INVALID_ARGUMENT;
     const size_t ns = (size_t)slices * p->V * p->N * sizeof(float);
     const size_t nv = (size_t)slices * p->N * p->N * sizeof(float);
     const uintptr_t a0 = (uintptr_t)d_sino, b0 = (uintptr_t)d_volume;

@@ -256,6 +256,7 @@ size_t brute_workspace_bytes(bst_plan_t p, int slices, int filtered) {
 
 static bst_status_t check_io(bst_plan_t p, const float* sino, int slices, const float* vol) {
     if (!p || !sino || !vol || slices <= 0) return BST_ERR_INVALID_ARGUMENT;
+    if (!bsth::on_plan_device(p)) return BST_ERR_INVALID_ARGUMENT;
     const size_t ns = (size_t)slices * p->V * p->N * sizeof(float);
     const size_t nv = (size_t)slices * p->N * p->N * sizeof(float);
     if (ranges_overlap(sino, ns, vol, nv)) return BST_ERR_INVALID_ARGUMENT;
@@ -308,6 +309,7 @@ bst_status_t bst_fbp_backward(bst_plan_t p, const float* d_sino, const float* d_
                               const float* d_g, float* d_grad_sino, float* d_grad_g, void* d_ws, size_t ws_bytes,
                               bst_stream_t stream) {
     if (!p || !d_grad_vol || slices <= 0 || (!d_grad_sino && !d_grad_g)) return BST_ERR_INVALID_ARGUMENT;
+    if (!bsth::on_plan_device(p)) return BST_ERR_INVALID_ARGUMENT;
     if (d_grad_g && !d_sino) return BST_ERR_INVALID_ARGUMENT;
     if (p->grid_kind != BST_GRID_BILINEAR) return BST_ERR_INVALID_ARGUMENT;
     const size_t nv = (size_t)slices * p->N * p->N * sizeof(float), ns = (size_t)slices * p->V * p->N * sizeof(float);
@@ -335,6 +337,7 @@ int bst_plan_get_schedule(bst_plan_t p) { return p ? p->maxr : 0; }
 
 bst_status_t bst_plan_autotune(bst_plan_t p, int slices, int* chosen) {
     if (!p) return BST_ERR_INVALID_ARGUMENT;
+    if (!bsth::on_plan_device(p)) return BST_ERR_INVALID_ARGUMENT;
     if (slices <= 0) {
         const size_t per = (size_t)p->V * p->N * sizeof(float);
         slices = (int)std::max<size_t>(2, std::min<size_t>(4096, (((size_t)256 << 20) / per) & ~(size_t)1));

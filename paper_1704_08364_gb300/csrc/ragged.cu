@@ -219,7 +219,7 @@ bst_status_t bst_ragged_create(bst_ragged_t* out, int items, const bst_plan_t* p
     *out = nullptr;
     if (items <= 0 || !plans) return BST_ERR_INVALID_ARGUMENT;
     for (int i = 0; i < items; ++i) {
-        if (!plans[i]) return BST_ERR_INVALID_ARGUMENT;
+        if (!plans[i] || !bsth::on_plan_device(plans[i])) return BST_ERR_INVALID_ARGUMENT;
         if (!bst::ragged_supported(plans[i]->M)) return BST_ERR_UNSUPPORTED_SIZE;
     }
     bst_ragged_s* r = new (std::nothrow) bst_ragged_s();
@@ -285,6 +285,7 @@ int bst_ragged_pair_items(bst_ragged_t r) { return r ? (int)r->first.size() : 0;
 bst_status_t bst_ragged_bind(bst_ragged_t r, const float* const* d_sinos, const float* const* d_g,
                              float* const* d_volumes, void* d_ws, size_t ws_bytes, int flags) {
     if (!r || !d_sinos || !d_volumes) return BST_ERR_INVALID_ARGUMENT;
+    if (!bsth::on_plan_device(r->plans[0])) return BST_ERR_INVALID_ARGUMENT;
     if (!d_ws || ws_bytes < bst_ragged_workspace_bytes(r)) return BST_ERR_WORKSPACE_TOO_SMALL;
     for (int i = 0; i < r->items; ++i)
         if (!d_sinos[i] || !d_volumes[i]) return BST_ERR_INVALID_ARGUMENT;
@@ -370,6 +371,7 @@ bst_status_t bst_ragged_set_spin_limit(bst_ragged_t r, int iterations) {
 
 bst_status_t bst_ragged_fbp(bst_ragged_t r, int use_graph, bst_stream_t stream) {
     if (!r || !r->bound) return BST_ERR_INVALID_ARGUMENT;
+    if (!bsth::on_plan_device(r->plans[0])) return BST_ERR_INVALID_ARGUMENT;
     cudaStream_t st = (cudaStream_t)stream;
     if (!use_graph) return enqueue(r, st);
     if (!r->exec) {
