@@ -61,3 +61,11 @@ def test_invalid_arguments_need_no_device(lib):
     assert L.bst_fbp_backward(None, None, None, 1, None, None, None, None, 0, None) == 1
     k, w = ctypes.c_int(0), ctypes.c_int(0)
     assert L.bst_plan_get_gridding(None, ctypes.byref(k), ctypes.byref(w)) == 1
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No fallback: the binding raises when the compiled library is absent."""
+    from paper_1704_08364_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        _lib.load(str(tmp_path / "libbst.so"))
