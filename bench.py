@@ -144,15 +144,37 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def oracle_slice_time(N: int, V: int, slices: int = 1):
-    """Time the FP64 oracle (BST FBP) on `slices` host-generated slices."""
+def oracle_slice_time(N: int, V: int, slices: int = 1, alpha: int = 2, kb_width: int = 0):
+    """Time the FP64 oracle (BST FBP, bilinear or KB gridding) on `slices`
+    host-generated slices."""
     import synth
     from oracle import bst as ob
+    from oracle import kb as okb
     theta, sino, _ = synth.workload_slices("volume-2048", list(range(slices)), rays=N, angles=V)
     t0 = time.perf_counter()
     for s in range(slices):
-        ob.fbp(sino[s].astype(np.float64), theta)
+        y = sino[s].astype(np.float64)
+        if kb_width:
+            okb.kb_fbp(y, theta, alpha, width=kb_width)
+        else:
+            ob.fbp(y, theta, alpha)
     return time.perf_counter() - t0
+
+
+L2_BYTES = 126 << 20   # GB300 L2 (about 129 MB)
+
+
+def workload_config(args, world: int) -> dict:
+    """The `config` of the JSON line, the same for both arms."""
+    N = V = args.rays
+    S, alpha = args.slices, args.pad
+    kbw = args.kb_width if args.gridding == "kb" else 0
+    return {"workload": f"volume-{N} ({S} slices x {V} angles x {N} rays FP32, pad {alpha}, M={alpha * N})",
+            "gridding": f"kaiser-bessel W={kbw}" if kbw else "bilinear",
+            "slices_per_gpu": S,
+            "l2": ("inputs (%.1f GiB) larger than L2" if S * V * N * 4 > L2_BYTES else
+                   "inputs (%.3f GiB) fit in L2: no flush between steps") % (S * V * N * 4 / 2**30),
+            "parallelism": f"slices, {world} GPU(s), weak"}
 
 
 def _event_ms(fn, steps, warmup=2):
@@ -283,19 +305,19 @@ def run_reference(args, rank, world):
     N = V = args.rays
     if rank != 0:
         return
+    kbw = args.kb_width if args.gridding == "kb" else 0
     for _ in range(args.warmup):
-        oracle_slice_time(N, V, 1)
-    times = [oracle_slice_time(N, V, 1) for _ in range(args.steps)]
+        oracle_slice_time(N, V, 1, args.pad, kbw)
+    times = [oracle_slice_time(N, V, 1, args.pad, kbw) for _ in range(args.steps)]
     per_step = float(np.mean(times))
     value = N * N / per_step
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "volume-2048 (2048 slices x 2048 angles x 2048 rays FP32, pad 2)",
-                   "step": "one slice of the workload through the FP64 numpy oracle"},
+        "config": workload_config(args, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "1 slice (2048 x 2048) per step, FP64 numpy oracle, single-threaded"},
+                         "sample": f"1 slice ({N} x {N}) of the workload per step, FP64 numpy oracle, single-threaded"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -452,7 +474,7 @@ def run_ours(args, rank, world):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         ns = 2
-        t = oracle_slice_time(N, V, ns)
+        t = oracle_slice_time(N, V, ns, alpha, kbw)
         cpu = {"value": ns * N * N / t, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{ns} slices of {N}x{N} (same workload), FP64 numpy oracle BST FBP, single-threaded"}
 
@@ -462,10 +484,7 @@ def run_ours(args, rank, world):
             "warmup": args.warmup, "ms_per_step": ms, "median_step_ms": statistics.median(step_ms),
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"volume-{N} ({S} slices x {V} angles x {N} rays FP32, pad {alpha}, M={M})",
-                       "gridding": f"kaiser-bessel W={kbw}" if kbw else "bilinear",
-                       "slices_per_gpu": S, "l2": "inputs (%.1f GiB) larger than L2" % (S * V * N * 4 / 2**30),
-                       "parallelism": f"slices, {world} GPU(s), weak"},
+            "config": workload_config(args, world),
             "slices_per_s": world * S / (ms / 1e3),
             "roofline": roofline, "path_hbm": path_hbm,
             "vs_brute": {"brute_ms_per_slice": brute_ms_per_slice, "bst_ms_per_slice": bst_ms_per_slice,
