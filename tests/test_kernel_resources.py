@@ -1,0 +1,51 @@
+"""Register and spill budget of the 2048^3 forward kernels, read from ptxas
+(-Xptxas -v) at compile time; no GPU needed.  A regression guard: the gridding
+kernel runs four 256-thread blocks per SM (64 registers a thread) and its
+measured-best form spills 24 bytes; the FFT kernels spill nothing."""
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+NVCC = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+
+
+@pytest.fixture(scope="module")
+def report(tmp_path_factory):
+    nvcc = NVCC if os.path.exists(NVCC) else shutil.which("nvcc")
+    if not nvcc:
+        pytest.skip("nvcc not available")
+    out = tmp_path_factory.mktemp("ptxas") / "k.o"
+    r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-Xptxas", "-v",
+                        "-I", os.path.join(ROOT, "paper_1704_08364_gb300", "csrc"),
+                        "-I", os.path.join(ROOT, "include"),
+                        "-c", os.path.join(ROOT, "tests", "kernel_resources.cu"), "-o", str(out)],
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    txt = r.stdout + r.stderr
+    res = {}
+    # one block per kernel, from its "Compiling entry function" line to the next
+    for block in txt.split("Compiling entry function")[1:]:
+        for name in ("k_ray_fft", "k_grid_col", "k_row_ifft"):
+            if re.match(r"\s*'[^']*" + name + r"ILi4096", block):
+                regs = re.search(r"Used (\d+) registers", block)
+                spill = re.search(r"(\d+) bytes spill stores", block)
+                assert regs and spill, block
+                res[name] = (int(regs.group(1)), int(spill.group(1)))
+    assert sorted(res) == ["k_grid_col", "k_ray_fft", "k_row_ifft"], txt
+    return res
+
+
+def test_fft_kernels_do_not_spill(report):
+    for name in ("k_ray_fft", "k_row_ifft"):
+        regs, spill = report[name]
+        assert spill == 0, f"{name} spills {spill} bytes"
+
+
+def test_gridding_kernel_keeps_four_blocks_per_sm(report):
+    regs, spill = report["k_grid_col"]
+    assert regs <= 64, f"k_grid_col uses {regs} registers"
+    assert spill <= 32, f"k_grid_col spills {spill} bytes"
