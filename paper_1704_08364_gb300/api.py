@@ -400,3 +400,74 @@ class RaggedBatch:
     def status(self) -> int:
         """Synchronise; return (and clear) the device status code (0 = ok)."""
         return int(self._lib.bst_ragged_status(self._h, _stream()))
+
+
+# ---------------------------------------------------------------------------
+# Module-level calls: each takes the geometry with the data, builds the plan on
+# first use (one per device, ray count, angle list and pad factor, kept until
+# clear_plans()) and calls that plan's method.
+
+_PLANS: dict = {}
+
+
+def _device_index() -> int:
+    return torch.cuda.current_device()
+
+
+def plan_for(rays: int, angles, pad_factor: int = 2) -> Plan:
+    """The cached plan of this geometry on the current device."""
+    th = np.ascontiguousarray(np.asarray(angles, dtype=np.float32))
+    key = (_device_index(), int(rays), int(pad_factor), th.tobytes())
+    plan = _PLANS.get(key)
+    if plan is None:
+        plan = _PLANS[key] = Plan(rays, th, pad_factor)
+    return plan
+
+
+def clear_plans():
+    """Drop the cached plans (and their device tables)."""
+    _PLANS.clear()
+
+
+def fbp(sino, angles, pad_factor: int = 2, g=None, out=None):
+    """BST filtered backprojection of sino [S][V][N] (or [V][N]) at the angles
+    theta_j (radians, [0, pi), increasing) -> volume [S][N][N]."""
+    return plan_for(sino.shape[-1], angles, pad_factor).fbp(sino, g=g, out=out)
+
+
+def backproject(sino, angles, pad_factor: int = 2, out=None):
+    """Plain BST backprojection b = B y (Eq. 2 through Eq. 3), defined up to a
+    constant (zero DC)."""
+    return plan_for(sino.shape[-1], angles, pad_factor).backproject(sino, out=out)
+
+
+def radon_adjoint(vol, angles, mode: int = FILTER, g=None, pad_factor: int = 2, out=None):
+    """Transpose of fbp (mode FILTER, taps g) or of backproject (mode
+    BACKPROJECT): volume [S][N][N] -> sinogram [S][V][N]."""
+    return plan_for(vol.shape[-1], angles, pad_factor).radon_adjoint(vol, mode=mode, g=g, out=out)
+
+
+def brute_backproject(sino, angles, g=None, pad_factor: int = 2, out=None):
+    """Slant-stack backprojection (Eq. 2), the O(N^3) comparator; with taps g
+    the slant-stack filtered backprojection."""
+    return plan_for(sino.shape[-1], angles, pad_factor).brute_backproject(sino, g=g, out=out)
+
+
+def fbp_ragged(sinos, angles=None, pad_factor: int = 2, gs=None, use_graph: bool = False):
+    """BST FBP of sinograms of mixed sizes (sinos[i]: [V_i][N_i]) in one
+    persistent launch.  angles[i] are item i's angles (default j pi / V_i);
+    items with the same geometry share a plan and are paired.  Blocks until
+    the launch is done and returns the volumes [N_i][N_i]."""
+    n = len(sinos)
+    if angles is None:
+        angles = [np.arange(s.shape[0], dtype=np.float64) * np.pi / s.shape[0] for s in sinos]
+    if len(angles) != n:
+        raise ValueError("one angle list per sinogram")
+    plans = [plan_for(s.shape[-1], a, pad_factor) for s, a in zip(sinos, angles)]
+    vols = [torch.empty((p.rays, p.rays), dtype=torch.float32, device=s.device) for p, s in zip(plans, sinos)]
+    batch = RaggedBatch(plans).bind(list(sinos), vols, gs)
+    batch.run(use_graph)
+    code = batch.status()
+    if code != 0:
+        raise BstError(code, "bst_ragged_fbp")
+    return vols
