@@ -38,10 +38,21 @@ def normalize(counts, flat, dark=None) -> np.ndarray:
 
 
 def kaiser_bessel(t, beta: float, half: float) -> np.ndarray:
+    """w(t) = I0(beta sqrt(1 - (t/half)^2)) / I0(beta) on |t| <= half, else 0 (stage P1)."""
     t = np.asarray(t, dtype=np.float64)
     inside = np.abs(t) <= half
     arg = beta * np.sqrt(np.maximum(1.0 - (t / half) ** 2, 0.0))
     return np.where(inside, np.i0(arg) / np.i0(beta), 0.0)
+
+
+def window_on_measured(N: int, shift: float, beta: float, half: float) -> np.ndarray:
+    """The P1 window at the measured detector samples t_i = (i - N/2) dt.
+
+    The window is centred on the rotation axis (Sec. 1 (b)): a measured
+    sample at t_i sits at t_i - shift*dt in centred coordinates, so it is
+    weighted by w(t_i - shift*dt)."""
+    t = (np.arange(N) - N // 2) * (2.0 / N)
+    return kaiser_bessel(t - shift * (2.0 / N), beta, half)
 
 
 def prepared_fbp(sino, angles, pad_factor: int = 2, g=None, flat=None, dark=None, shift: float = 0.0,
@@ -56,8 +67,7 @@ def prepared_fbp(sino, angles, pad_factor: int = 2, g=None, flat=None, dark=None
     M = pad_factor * N
     y = normalize(s, flat, dark) if flat is not None else s
     if kb_beta > 0.0:
-        t = (np.arange(N) - N // 2) * (2.0 / N)
-        y = y * kaiser_bessel(t - shift * (2.0 / N), kb_beta, kb_half)[None, :]
+        y = y * window_on_measured(N, shift, kb_beta, kb_half)[None, :]
     Y = ob.ray_spectrum(y, M)
     if shift != 0.0:
         Y = Y * np.exp(2j * np.pi * ob.signed_index(M) * shift / M)[None, :]

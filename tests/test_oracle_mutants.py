@@ -59,6 +59,10 @@ def test_pins_pass_on_the_real_oracle():
     from test_oracle_bst import linear_spectrum_error
     th = np.sort(np.random.default_rng(2).uniform(0.03, 3.1, 40)).astype(np.float32)
     assert linear_spectrum_error(th) <= 0.0
+    from test_oracle_prep import shifted_window_error, window_peak_error, window_transform_error
+    assert window_transform_error() < 1e-12
+    assert window_peak_error() < 1e-15
+    assert shifted_window_error() < 1e-12
 
 
 def _swap_taps(pairs):
@@ -118,3 +122,29 @@ def test_planted_mistake_is_caught(name, monkeypatch):
         from test_oracle_bst import linear_spectrum_error
         th = np.sort(np.random.default_rng(2).uniform(0.03, 3.1, 40)).astype(np.float32)
         assert linear_spectrum_error(th) > 1.0
+
+
+@pytest.mark.parametrize("name", ["window_sqrt_dropped", "window_shift_sign_flipped",
+                                  "window_normalised_twice"])
+def test_planted_window_mistake_is_caught(name, monkeypatch):
+    """Stage P1 (Sec. 2) and its placement under centering (Sec. 1 (b))."""
+    from oracle import prep
+    from test_oracle_prep import shifted_window_error, window_peak_error, window_transform_error
+    if name == "window_sqrt_dropped":
+        def mutant(t, beta, half):
+            t = np.asarray(t, dtype=np.float64)
+            arg = beta * np.maximum(1.0 - (t / half) ** 2, 0.0)
+            return np.where(np.abs(t) <= half, np.i0(arg) / np.i0(beta), 0.0)
+        monkeypatch.setattr(prep, "kaiser_bessel", mutant)
+        assert window_transform_error() > 1e-3
+    elif name == "window_shift_sign_flipped":
+        def mutant(N, shift, beta, half):
+            t = (np.arange(N) - N // 2) * (2.0 / N)
+            return prep.kaiser_bessel(t + shift * (2.0 / N), beta, half)
+        monkeypatch.setattr(prep, "window_on_measured", mutant)
+        assert shifted_window_error() > 1e-2
+    elif name == "window_normalised_twice":
+        real = prep.kaiser_bessel
+        monkeypatch.setattr(prep, "kaiser_bessel", lambda t, beta, half: real(t, beta, half) / np.i0(beta))
+        assert window_peak_error() > 0.1
+        assert window_transform_error() > 1e-3
