@@ -6,13 +6,21 @@ resident in HBM.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Multi-GPU (torchrun, one rank per GPU): every rank reconstructs its own
-volume of the same size (weak scaling, no collective on the data path); the
-timed region is bracketed by barriers and the slowest rank's time is used.
+Multi-GPU (torchrun, one rank per GPU): by default every rank reconstructs
+its own volume of the same size (weak scaling: slices are independent, so the
+path shards with no collective on the data path).  --scaling strong instead
+splits ONE volume of --slices slices into contiguous whole-pair ranges, one
+per rank (the distribution of blocks of slices over GPUs of Sec. 3), again
+with no data-path collective.  Either way the timed region is bracketed by
+barriers and the slowest rank's time is used.
 
---impl reference times the FP64 CPU oracle (the plain restatement of the
-method used by the tests) on the host cores, on a bounded sample of the same
-workload (one slice per step).
+CPU baseline (`cpu_baseline`, rank 0 at one GPU) and --impl reference: the
+FP64 CPU oracle (the plain restatement of the method used by the tests), as
+it stands, on all host cores: one spawned single-threaded worker process per
+core (capped by the host memory, about 1.5 GB per worker at 2048 rays), each
+reconstructing one slice of the same workload, all started together; the
+throughput is the slices done divided by the wall time from the common start
+to the last finish.  The worker count is reported as `cores`.
 """
 from __future__ import annotations
 
@@ -56,6 +64,17 @@ def fft_flops(M: int) -> float:
 def disk_points(M: int) -> int:
     k = np.arange(M) - M // 2
     return int(np.count_nonzero(k[None, :] ** 2 + k[:, None] ** 2 < (M // 2) ** 2))
+
+
+def stage_bytes(N: int, V: int, M: int) -> dict:
+    """Compulsory DRAM bytes per launch (one slice pair) of each forward
+    kernel: its own input read once and its output written once.  The ray
+    kernel reads two slices' sinograms and writes Z (V x M complex64); the
+    gridding kernel reads Z and writes T (4 ceil(N/4) x M complex64); the row
+    kernel reads T and writes two slices' images."""
+    z = V * M * 8
+    t = 4 * ((N + 3) // 4) * M * 8
+    return {0: 2 * V * N * 4 + z, 1: z + t, 2: t + 2 * N * N * 4}
 
 
 def stage_flops(N: int, V: int, M: int, kb_width: int = 0) -> dict:
@@ -144,24 +163,82 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def oracle_slice_time(N: int, V: int, slices: int = 1, alpha: int = 2, kb_width: int = 0):
-    """Time the FP64 oracle (BST FBP, bilinear or KB gridding) on `slices`
-    host-generated slices."""
+def _oracle_worker(idx, N, V, alpha, kb_width, barrier, out):
+    """One spawned worker: generate its slice, wait for the common start,
+    reconstruct it with the FP64 oracle, report the finish time."""
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
     import synth
     from oracle import bst as ob
     from oracle import kb as okb
-    theta, sino, _ = synth.workload_slices("volume-2048", list(range(slices)), rays=N, angles=V)
-    t0 = time.perf_counter()
-    for s in range(slices):
-        y = sino[s].astype(np.float64)
-        if kb_width:
-            okb.kb_fbp(y, theta, alpha, width=kb_width)
-        else:
-            ob.fbp(y, theta, alpha)
-    return time.perf_counter() - t0
+    theta, sino, _ = synth.workload_slices("volume-2048", [idx], rays=N, angles=V)
+    y = sino[0].astype(np.float64)
+    barrier.wait()
+    if kb_width:
+        okb.kb_fbp(y, theta, alpha, width=kb_width)
+    else:
+        ob.fbp(y, theta, alpha)
+    out.put(time.time())
+
+
+def oracle_workers(N: int) -> int:
+    """Worker processes for the oracle timing: every host core, capped so that
+    the workers (about 1.5 GB each at 2048 rays, scaling with N^2) fit in half
+    of the available host memory."""
+    cores = os.cpu_count() or 1
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError, AttributeError):
+        return cores
+    per = max(1.6e9 * (N / 2048.0) ** 2, 5e7)
+    return max(1, min(cores, int(0.5 * avail / per)))
+
+
+class OraclePool:
+    """Times the FP64 oracle on `workers` slices reconstructed concurrently by
+    as many spawned single-threaded processes (spawned, never forked, so that
+    a CUDA context of the parent is not inherited)."""
+
+    def __init__(self, N: int, V: int, alpha: int = 2, kb_width: int = 0, workers: int | None = None):
+        self.N, self.V, self.alpha, self.kb_width = N, V, alpha, kb_width
+        self.workers = workers or oracle_workers(N)
+
+    def run(self) -> float:
+        """Wall seconds from the common start to the last worker's finish."""
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        barrier = ctx.Barrier(self.workers + 1)
+        out = ctx.Queue()
+        procs = [ctx.Process(target=_oracle_worker, args=(i, self.N, self.V, self.alpha, self.kb_width,
+                                                          barrier, out)) for i in range(self.workers)]
+        for p in procs:
+            p.start()
+        barrier.wait()
+        t0 = time.time()
+        finish = [out.get() for _ in procs]
+        for p in procs:
+            p.join()
+        if any(p.exitcode != 0 for p in procs):
+            raise RuntimeError("an oracle worker failed")
+        return max(finish) - t0
+
+    def sample(self) -> str:
+        g = f"kaiser-bessel W={self.kb_width}" if self.kb_width else "bilinear"
+        return (f"{self.workers} slices of {self.N}x{self.N} ({self.V} angles, pad {self.alpha}, {g}) of the same "
+                f"workload, one per worker process, reconstructed concurrently by the FP64 numpy oracle")
 
 
 L2_BYTES = 126 << 20   # GB300 L2 (about 129 MB)
+
+
+def rank_slices(args, rank: int, world: int) -> tuple[int, int]:
+    """[start, stop) of the workload's slices that this rank reconstructs per
+    step: the whole volume (weak scaling) or its contiguous whole-pair share of
+    one volume (strong scaling)."""
+    if args.scaling == "strong" and world > 1:
+        from paper_1704_08364_gb300.shard import slice_range
+        return slice_range(rank, world, args.slices)
+    return 0, args.slices
 
 
 def workload_config(args, world: int) -> dict:
@@ -169,12 +246,15 @@ def workload_config(args, world: int) -> dict:
     N = V = args.rays
     S, alpha = args.slices, args.pad
     kbw = args.kb_width if args.gridding == "kb" else 0
+    strong = args.scaling == "strong" and world > 1
+    per_gpu = (S + world - 1) // world if strong else S
     return {"workload": f"volume-{N} ({S} slices x {V} angles x {N} rays FP32, pad {alpha}, M={alpha * N})",
             "gridding": f"kaiser-bessel W={kbw}" if kbw else "bilinear",
-            "slices_per_gpu": S,
-            "l2": ("inputs (%.1f GiB) larger than L2" if S * V * N * 4 > L2_BYTES else
-                   "inputs (%.3f GiB) fit in L2: no flush between steps") % (S * V * N * 4 / 2**30),
-            "parallelism": f"slices, {world} GPU(s), weak"}
+            "slices_per_gpu": per_gpu,
+            "l2": ("inputs (%.1f GiB) larger than L2" if per_gpu * V * N * 4 > L2_BYTES else
+                   "inputs (%.3f GiB) fit in L2: no flush between steps") % (per_gpu * V * N * 4 / 2**30),
+            "parallelism": (f"slices, {world} GPU(s), one volume split in whole-pair ranges" if strong else
+                            f"slices, {world} GPU(s), one volume per GPU")}
 
 
 def _event_ms(fn, steps, warmup=2):
@@ -306,18 +386,19 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     kbw = args.kb_width if args.gridding == "kb" else 0
+    pool = OraclePool(N, V, args.pad, kbw, min(oracle_workers(N), max(1, args.slices)))
     for _ in range(args.warmup):
-        oracle_slice_time(N, V, 1, args.pad, kbw)
-    times = [oracle_slice_time(N, V, 1, args.pad, kbw) for _ in range(args.steps)]
+        pool.run()
+    times = [pool.run() for _ in range(args.steps)]
     per_step = float(np.mean(times))
-    value = N * N / per_step
+    value = pool.workers * N * N / per_step
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args, world),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"1 slice ({N} x {N}) of the workload per step, FP64 numpy oracle, single-threaded"},
+        "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(args, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.workers, "host_cores": os.cpu_count(),
+                         "kind": "oracle", "sample": pool.sample() + " (one such batch per step)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -335,7 +416,9 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     N = V = args.rays
-    S = args.slices
+    s0, s1 = rank_slices(args, rank, world)
+    S = s1 - s0                       # slices this rank reconstructs per step
+    total_slices = args.slices if args.scaling == "strong" else world * S
     alpha = args.pad
     theta = synth.uniform_angles(V)
     plan = bst.Plan(N, theta, alpha)
@@ -343,7 +426,10 @@ def run_ours(args, rank, world):
     if kbw:
         plan.set_gridding("kaiser-bessel", kbw)
     M = plan.M
-    sino = sdev.ellipse_volume(synth.WORKLOADS["volume-2048"].index, S, V, N, noise_frac=0.01, device=dev)
+    # this rank's slices of the workload (the generator seeds each slice by its
+    # index; the strong-scaling ranges are regenerated from the same seeds)
+    sino = sdev.ellipse_volume(synth.WORKLOADS["volume-2048"].index, S, V, N, noise_frac=0.01, device=dev,
+                               first_slice=s0)
     vol = torch.empty((S, N, N), dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
 
@@ -375,7 +461,7 @@ def run_ours(args, rank, world):
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * S * N * N / (ms / 1e3)
+    value = total_slices * N * N / (ms / 1e3)
 
     # end to end through the C-ABI host entry point: the step's input in pinned
     # host memory, uploads / kernels / downloads overlapped in chunks, the
@@ -405,8 +491,8 @@ def run_ours(args, rank, world):
             t = torch.tensor([dt], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             dt = float(t.item())
-        e2e = {"value": world * es * N * N / dt, "unit": UNIT, "h2d_bytes_per_step": es * V * N * 4,
-               "d2h_bytes_per_step": es * N * N * 4, "slices": es, "ms_per_step": dt * 1e3,
+        e2e = {"value": world * es * N * N / dt, "unit": UNIT, "h2d_bytes_per_step": world * es * V * N * 4,
+               "d2h_bytes_per_step": world * es * N * N * 4, "slices": world * es, "ms_per_step": dt * 1e3,
                "best_ms": 1e3 * min(per_step), "worst_ms": 1e3 * max(per_step),
                "api": "bst_fbp_host (pinned host buffers, chunked copy/compute overlap)"}
         del h_in, h_out
@@ -435,16 +521,33 @@ def run_ours(args, rank, world):
     peak_tf = fp32_peak_tflops(sm_max)
     achieved_tf = flops[dom] / (avg_ms / 1e3) / 1e12
     traffic = None if kbw else captured_traffic(names[dom], N, alpha)
-    roofline = {"bound": "alu", "kernel": names[dom], "achieved": achieved_tf, "peak": peak_tf,
-                "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
-                "traffic": traffic,
-                "dram_gbs": None if traffic is None else traffic / (avg_ms / 1e3) / 1e9,
-                "dram_frac_of_hbm_peak": None if traffic is None else traffic / (avg_ms / 1e3) / 1e9 / hbm_peak,
-                "traffic_note": "DRAM bytes per launch from one cold-cache ncu capture (null if the kernel changed)",
+    # the bound is whichever floor is higher for this kernel: its algorithmic
+    # flops at the FP32 peak, or its compulsory bytes (its own inputs and
+    # outputs read or written once) at the HBM peak
+    cbytes = stage_bytes(N, V, M)[dom]
+    alu_floor_us = flops[dom] / (peak_tf * 1e12) * 1e6
+    hbm_floor_us = cbytes / (hbm_peak * 1e9) * 1e6
+    if alu_floor_us >= hbm_floor_us:
+        roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                    "frac": achieved_tf / peak_tf}
+    else:
+        gbs = cbytes / (avg_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak}
+    roofline.update({
+        "kernel": names[dom], "traffic": traffic,
+        "alu_floor_us": alu_floor_us, "hbm_floor_us": hbm_floor_us, "avg_us": avg_ms * 1e3,
+        "alu": {"achieved_tflops": achieved_tf, "peak_tflops": peak_tf, "frac": achieved_tf / peak_tf,
                 "algorithmic_flops_per_launch": flops[dom],
-                "peak_source": "FP32 152 SM x 128 lanes x 2 x %.0f MHz (derived)" % sm_max,
-                "stage_share": {names[s]: stage_ms[s] / max(sum(stage_ms.values()), 1e-9) for s in stage_ms},
-                "stage_avg_us": {names[s]: 1e3 * stage_ms[s] / max(stage_n[s], 1) for s in stage_ms}}
+                "peak_source": "FP32 152 SM x 128 lanes x 2 x %.0f MHz (derived)" % sm_max},
+        "hbm": {"compulsory_bytes_per_launch": cbytes, "achieved_gbs": cbytes / (avg_ms / 1e3) / 1e9,
+                "peak_gbs": hbm_peak, "frac": cbytes / (avg_ms / 1e3) / 1e9 / hbm_peak,
+                "peak_source": f"MEASURED_PEAKS hbm_gbs ({src})"},
+        "dram_gbs": None if traffic is None else traffic / (avg_ms / 1e3) / 1e9,
+        "dram_frac_of_hbm_peak": None if traffic is None else traffic / (avg_ms / 1e3) / 1e9 / hbm_peak,
+        "traffic_note": "DRAM bytes per launch from one cold-cache ncu capture of the current device code "
+                        "(null if it changed since)",
+        "stage_share": {names[s]: stage_ms[s] / max(sum(stage_ms.values()), 1e-9) for s in stage_ms},
+        "stage_avg_us": {names[s]: 1e3 * stage_ms[s] / max(stage_n[s], 1) for s in stage_ms}})
     alg_bytes = 4.0 * (V * N + N * N) * S
     path_hbm = {"algorithmic_bytes_per_step": alg_bytes, "achieved_gbs": alg_bytes / (ms / 1e3) / 1e9,
                 "peak_gbs": hbm_peak, "frac": alg_bytes / (ms / 1e3) / 1e9 / hbm_peak, "peak_source": src}
@@ -473,19 +576,19 @@ def run_ours(args, rank, world):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        ns = 2
-        t = oracle_slice_time(N, V, ns, alpha, kbw)
-        cpu = {"value": ns * N * N / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{ns} slices of {N}x{N} (same workload), FP64 numpy oracle BST FBP, single-threaded"}
+        pool = OraclePool(N, V, alpha, kbw)
+        t = pool.run()
+        cpu = {"value": pool.workers * N * N / t, "unit": UNIT, "cores": pool.workers,
+               "host_cores": os.cpu_count(), "kind": "oracle", "seconds": t, "sample": pool.sample()}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "median_step_ms": statistics.median(step_ms),
-            "higher_is_better": True, "scaling": "weak",
+            "higher_is_better": True, "scaling": args.scaling,
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args, world),
-            "slices_per_s": world * S / (ms / 1e3),
+            "slices_per_s": total_slices / (ms / 1e3),
             "roofline": roofline, "path_hbm": path_hbm,
             "vs_brute": {"brute_ms_per_slice": brute_ms_per_slice, "bst_ms_per_slice": bst_ms_per_slice,
                          "speedup": brute_ms_per_slice / bst_ms_per_slice, "brute_slices_timed": bs},
@@ -512,6 +615,8 @@ def main():
     ap.add_argument("--gridding", default="bilinear", choices=["bilinear", "kb"],
                     help="interpolation kernel of stage P5 for the main step (kb: Kaiser-Bessel)")
     ap.add_argument("--kb-width", type=int, default=6)
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="with several GPUs: one volume per GPU (weak) or one volume split over the GPUs (strong)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -71,13 +71,17 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
+// counter of element pair e: e + pair0, pair0 = the pairs of the slices before
+// this block, so that a block of slices gets the same noise as those slices of
+// the whole volume
 __global__ void k_add_noise(float* __restrict__ y, int V, int N, int S, const float* __restrict__ smax, float frac,
-                            unsigned long long seed) {
+                            unsigned long long seed, unsigned long long pair0) {
     const size_t per_slice = (size_t)V * N;
     const size_t total = per_slice * S;
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; 2 * e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)e, (uint32_t)(e >> 32), 0x5eedu, 0u), key);
+        const unsigned long long c = e + pair0;
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), 0x5eedu, 0u), key);
         const float u1 = ((float)(r.x >> 8) + 1.f) * (1.f / 16777216.f);
         const float u2 = (float)(r.y >> 8) * (1.f / 16777216.f);
         const float rad = sqrtf(-2.f * logf(u1));
@@ -108,12 +112,15 @@ int synth_ellipse_sinogram(const float* ell, const int* cnt, int kmax, const flo
 }
 
 // y += N(0, (frac * max|y_s|)^2) per slice s; smax_scratch: S floats of device memory.
-int synth_add_gaussian_noise(float* y, int S, int V, int N, float frac, unsigned long long seed, float* smax_scratch,
-                             void* stream) {
-    if (!y || !smax_scratch || S <= 0 || V <= 0 || N <= 0) return 1;
+// first_slice: index of y's first slice in the whole volume (first_slice * V * N even).
+int synth_add_gaussian_noise(float* y, int S, int V, int N, float frac, unsigned long long seed, long long first_slice,
+                             float* smax_scratch, void* stream) {
+    if (!y || !smax_scratch || S <= 0 || V <= 0 || N <= 0 || first_slice < 0) return 1;
+    const unsigned long long before = (unsigned long long)first_slice * V * N;
+    if (before & 1) return 1;
     cudaStream_t st = (cudaStream_t)stream;
     k_slice_absmax<<<S, 1024, 0, st>>>(y, (size_t)V * N, smax_scratch);
-    k_add_noise<<<152 * 16, 256, 0, st>>>(y, V, N, S, smax_scratch, frac, seed);
+    k_add_noise<<<152 * 16, 256, 0, st>>>(y, V, N, S, smax_scratch, frac, seed, before / 2);
     return cudaGetLastError() == cudaSuccess ? 0 : 2;
 }
 

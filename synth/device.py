@@ -26,18 +26,22 @@ def _load():
                                                ctypes.c_void_p]
         lib.synth_add_gaussian_noise.restype = ctypes.c_int
         lib.synth_add_gaussian_noise.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                                 ctypes.c_float, ctypes.c_ulonglong, ctypes.c_void_p,
-                                                 ctypes.c_void_p]
+                                                 ctypes.c_float, ctypes.c_ulonglong, ctypes.c_longlong,
+                                                 ctypes.c_void_p, ctypes.c_void_p]
         _lib = lib
     return _lib
 
 
 def ellipse_volume(config_index: int, slices: int, angles: int, rays: int, noise_frac: float = 0.0,
-                   device="cuda", out=None, kmax: int = 20) -> torch.Tensor:
+                   device="cuda", out=None, kmax: int = 20, first_slice: int = 0) -> torch.Tensor:
     """[slices][angles][rays] float32 sinograms of seeded random ellipse phantoms
-    (same per-slice seeds as the host generator), generated on the device."""
+    (same per-slice seeds as the host generator), generated on the device.
+    ``first_slice``: the index of the first slice in the whole volume; the
+    slices and their noise equal those slices of the whole volume generated
+    at once (first_slice * angles * rays must be even)."""
     lib = _load()
-    lists = [random_ellipses(np.random.default_rng(slice_seed(config_index, s))) for s in range(slices)]
+    lists = [random_ellipses(np.random.default_rng(slice_seed(config_index, first_slice + s)))
+             for s in range(slices)]
     tab, cnt = ellipse_table(lists, kmax)
     d_tab = torch.from_numpy(tab).to(device)
     d_cnt = torch.from_numpy(cnt).to(device)
@@ -52,7 +56,7 @@ def ellipse_volume(config_index: int, slices: int, angles: int, rays: int, noise
     if noise_frac > 0:
         smax = torch.empty((slices,), dtype=torch.float32, device=device)
         rc = lib.synth_add_gaussian_noise(out.data_ptr(), slices, angles, rays, float(noise_frac),
-                                          slice_seed(config_index, 0), smax.data_ptr(), st)
+                                          slice_seed(config_index, 0), first_slice, smax.data_ptr(), st)
         if rc:
             raise RuntimeError(f"synth_add_gaussian_noise failed ({rc})")
     return out

@@ -114,6 +114,43 @@ def test_volume_2048_sampled_slices(bst):
         assert_parity(got[n], ob.fbp(sub[n].astype(np.float64), theta), what=f"volume-2048 slice {s}")
 
 
+def test_paper_real_data_geometry_2048_rays_2000_angles(bst):
+    """The geometry of the paper's beamline runs (Sec. 4: N = 2048 rays,
+    V = 2000 angles), as one 2048-slice call in the benchmark's launch
+    configuration; two sampled slice pairs against the oracle."""
+    free, _ = torch.cuda.mem_get_info()
+    if free < 72 * 2**30:
+        pytest.skip("needs ~70 GiB of free device memory")
+    N, V = 2048, 2000
+    idx = [0, 1, 1500, 1501]
+    theta, sub, _ = synth.workload_slices("volume-2048", idx, angles=V)
+    plan = bst.Plan(N, theta, 2)
+    d = torch.zeros((2048, V, N), dtype=torch.float32, device="cuda")
+    d[idx] = torch.from_numpy(sub).cuda()
+    out = plan.fbp(d)
+    plan.status()
+    got = out[idx].cpu().numpy()
+    del d, out
+    for n, s in enumerate(idx):
+        assert_parity(got[n], ob.fbp(sub[n].astype(np.float64), theta), what=f"(2048, 2000) slice {s}")
+
+
+def test_nonuniform_angles_at_2048(bst):
+    """Sorted random angles at N = V = 2048 (M = 4096): the bracket search of
+    the plan's angle table runs at radii up to 2048 bins, where the exact
+    polar coordinates matter most; one slice pair against the oracle."""
+    rng = np.random.default_rng(2048)
+    N = V = 2048
+    theta = np.unique(rng.uniform(0.004, np.pi - 0.002, V + 16).astype(np.float32))[:V]
+    theta = np.sort(theta)
+    assert theta.size == V and np.all(np.diff(theta) > 0)
+    sino = np.stack([synth.gaussian_noise(synth.ellipse_sinogram(synth.random_ellipses(rng), theta, N), rng)
+                     for _ in range(2)]).astype(np.float32)
+    got = _run(bst, sino, theta)
+    for s in range(2):
+        assert_parity(got[s], ob.fbp(sino[s].astype(np.float64), theta), what=f"nonuniform 2048 slice {s}")
+
+
 def test_host_pipeline_matches_device_path(bst):
     """bst_fbp_host (chunked upload / reconstruct / download overlap) gives the
     device path's result; 41 slices of 2048 x 2048 span two staging chunks and

@@ -137,7 +137,8 @@ def test_volume_2048_sampled_pixels_against_the_direct_sum(bst):
     """The 2048^3 workload with KB gridding in the benchmark's launch
     configuration: sampled slices regenerated on the host, sampled pixels
     against the direct polar sum that the gridding approximates (its error at
-    W = 6 and pad factor 2 is ~2e-6 of the image scale)."""
+    W = 6 and pad factor 2 is ~2e-6 of the image scale), and one whole slice
+    against the KB oracle at the parity bar."""
     free, _ = torch.cuda.mem_get_info()
     if free < 72 * 2**30:
         pytest.skip("needs ~70 GiB of free device memory")
@@ -159,6 +160,8 @@ def test_volume_2048_sampled_pixels_against_the_direct_sum(bst):
         scale = float(np.abs(got[n]).max())
         err = np.abs(got[n][rows, cols] - ref).max()
         assert err <= 2e-5 * scale, f"slice {s}: max err {err:.3e} vs scale {scale:.3e}"
+    # the oracle the kernel implements, on one whole slice, at the path's parity bar
+    assert_parity(got[0], kb.kb_fbp(sub[0].astype(np.float64), theta), what="KB 2048 slice 0 vs kb_fbp")
 
 
 def test_host_pipeline_and_noalloc_on_a_kb_plan(bst):

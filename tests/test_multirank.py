@@ -70,3 +70,20 @@ def test_filter_gradient_allreduce_over_two_gloo_ranks(tmp_path):
     ref = sum(oa.filter_grad(p[s], R[s], theta) for s in range(6))
     for r in range(2):
         np.testing.assert_allclose(np.load(tmp_path / f"g{r}.npy"), ref, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 4, 8])
+def test_bench_strong_scaling_ranges_cover_one_volume_in_whole_pairs(world):
+    """bench.py --scaling strong: the ranks' slice ranges of one 2048-slice
+    volume tile it exactly, each starting on a pair boundary; weak scaling
+    gives every rank the whole volume."""
+    import argparse
+    import bench
+    args = argparse.Namespace(scaling="strong", slices=2048)
+    got = [bench.rank_slices(args, r, world) for r in range(world)]
+    assert got[0][0] == 0 and got[-1][1] == 2048
+    assert all(a1 == b0 for (_, a1), (b0, _) in zip(got, got[1:]))
+    assert all(a0 % 2 == 0 and (a1 - a0) % 2 == 0 for a0, a1 in got)
+    assert sum(a1 - a0 for a0, a1 in got) == 2048
+    weak = argparse.Namespace(scaling="weak", slices=2048)
+    assert all(bench.rank_slices(weak, r, world) == (0, 2048) for r in range(world))
