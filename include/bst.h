@@ -66,6 +66,25 @@ typedef enum {
     BST_GRID_KAISER_BESSEL = 1  /* KB convolution gridding with deapodization */
 } bst_gridding_t;
 
+/* Memory layout of the polar spectrum between the ray and gridding stages
+ * (an implementation choice; the paper's stages P3-P5 fix the values only). */
+typedef enum {
+    BST_LAYOUT_PACKED = 0,  /* Z[V][M] complex64, natural order of k */
+    BST_LAYOUT_PAIRED = 1   /* Z[V][M/2] pairs (Z[k], Z[-k]): one 16-byte load serves a
+                               Cartesian point and its mirror (bilinear gridding only) */
+} bst_layout_t;
+
+/* Launch shape of the forward path (extension; no passage: the paper fixes
+ * the stages, not how they are tiled).  Results are identical up to
+ * rounding whatever the shape. */
+typedef struct {
+    int max_radix;    /* largest Stockham radix: 16 or 8 */
+    int layout;       /* bst_layout_t */
+    int chunk_pairs;  /* slice pairs per launch of each stage, 1..256 */
+    int pair_fast;    /* 1: gridding blocks ordered pair-fastest within a chunk */
+    int max_lanes;    /* streams alternating chunks, 1 or 2 */
+} bst_fwd_config_t;
+
 typedef struct bst_plan_s* bst_plan_t;
 typedef void* bst_stream_t;   /* a cudaStream_t; NULL is the legacy default stream */
 
@@ -263,10 +282,27 @@ bst_status_t bst_plan_set_gridding(bst_plan_t plan, int kind, int width);
 /* The plan's gridding kind and width (2 for bilinear). Errors: INVALID_ARGUMENT. */
 bst_status_t bst_plan_get_gridding(bst_plan_t plan, int* kind, int* width);
 
-/* Autotuner: time the plan's forward path on a synthetic batch of about
- * 256 MiB (`slices` slices; <= 0 picks that size) with each radix schedule,
- * keep the faster one and return it in *chosen.  Allocates and frees its own
- * buffers; synchronises the device. */
+/* Launch shape of the plan's forward path (bst_fbp, bst_backproject,
+ * bst_fbp_prep, bst_fbp_host, bst_fbp_noalloc).  Extension; no passage.
+ * bst_plan_set_forward_config validates every field (max_radix 16 or 8,
+ * layout a bst_layout_t, chunk_pairs 1..256, pair_fast 0 or 1, max_lanes 1
+ * or 2) and changes nothing on error; bst_workspace_bytes follows the new
+ * chunk and lane counts, so size workspaces after setting it.  A plan starts
+ * with radix 16, the packed layout, chunks sized to about 64 MiB of
+ * workspace, block order column-fastest and two lanes.  A Kaiser-Bessel plan
+ * always uses the packed layout.  Errors: INVALID_ARGUMENT. */
+bst_status_t bst_plan_set_forward_config(bst_plan_t plan, const bst_fwd_config_t* config);
+bst_status_t bst_plan_get_forward_config(bst_plan_t plan, bst_fwd_config_t* config);
+
+/* Autotuner (extension; no passage): time the plan's forward path on a
+ * synthetic batch of about 256 MiB (`slices` slices, at least 4, and at
+ * least 64 where the default chunk is one pair; <= 0 picks that size) under
+ * each candidate launch shape -- radix 16 or 8; packed or
+ * paired layout (bilinear plans); the plan's default chunk and, where that
+ * is one pair, chunks of 2, 4 and 8 pairs; either block order -- keep the fastest
+ * (the best of three timed runs each, after one warm-up run) and return its
+ * radix in *chosen (may be NULL).  Allocates and frees its own buffers;
+ * synchronises the device. */
 bst_status_t bst_plan_autotune(bst_plan_t plan, int slices, int* chosen);
 
 /* ---- ragged batch: sinograms of mixed sizes in one persistent launch ----- */

@@ -10,6 +10,12 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbst.so")
 
+class FwdConfig(ctypes.Structure):
+    """bst_fwd_config_t: the launch shape of the forward path."""
+    _fields_ = [("max_radix", ctypes.c_int), ("layout", ctypes.c_int), ("chunk_pairs", ctypes.c_int),
+                ("pair_fast", ctypes.c_int), ("max_lanes", ctypes.c_int)]
+
+
 c_plan = ctypes.c_void_p
 c_ptr = ctypes.c_void_p
 c_int = ctypes.c_int
@@ -42,6 +48,8 @@ SIGNATURES = {
     "bst_plan_set_gridding": (c_int, [c_plan, c_int, c_int]),
     "bst_plan_get_gridding": (c_int, [c_plan, ctypes.POINTER(c_int), ctypes.POINTER(c_int)]),
     "bst_plan_autotune": (c_int, [c_plan, c_int, ctypes.POINTER(c_int)]),
+    "bst_plan_set_forward_config": (c_int, [c_plan, ctypes.POINTER(FwdConfig)]),
+    "bst_plan_get_forward_config": (c_int, [c_plan, ctypes.POINTER(FwdConfig)]),
     "bst_ragged_create": (c_int, [ctypes.POINTER(c_ptr), c_int, ctypes.POINTER(c_plan)]),
     "bst_ragged_workspace_bytes": (c_size, [c_ptr]),
     "bst_ragged_pair_items": (c_int, [c_ptr]),

@@ -110,6 +110,26 @@ class Plan:
         _check(self._lib.bst_plan_set_schedule(self._h, int(max_radix)), "bst_plan_set_schedule")
 
     @property
+    def forward_config(self) -> dict:
+        """Launch shape of the forward path (bst_plan_get_forward_config):
+        max_radix, layout ("packed" or "paired"), chunk_pairs, pair_fast, max_lanes."""
+        c = _lib.FwdConfig()
+        _check(self._lib.bst_plan_get_forward_config(self._h, ctypes.byref(c)), "bst_plan_get_forward_config")
+        return {"max_radix": c.max_radix, "layout": "paired" if c.layout == 1 else "packed",
+                "chunk_pairs": c.chunk_pairs, "pair_fast": c.pair_fast, "max_lanes": c.max_lanes}
+
+    def set_forward_config(self, **kw):
+        """Change fields of the launch shape (bst_plan_set_forward_config);
+        results are identical up to rounding whatever the shape."""
+        cur = self.forward_config
+        cur.update(kw)
+        layout = {"packed": 0, "paired": 1}.get(cur["layout"], cur["layout"])
+        c = _lib.FwdConfig(int(cur["max_radix"]), int(layout),
+                           int(cur["chunk_pairs"]), int(cur["pair_fast"]), int(cur["max_lanes"]))
+        _check(self._lib.bst_plan_set_forward_config(self._h, ctypes.byref(c)), "bst_plan_set_forward_config")
+        return self
+
+    @property
     def gridding(self) -> tuple[str, int]:
         """Interpolation kernel of stage P5: ("bilinear", 2) or ("kaiser-bessel", W)."""
         kind, width = ctypes.c_int(0), ctypes.c_int(0)
@@ -124,10 +144,12 @@ class Plan:
         _check(self._lib.bst_plan_set_gridding(self._h, k, int(width)), "bst_plan_set_gridding")
         return self
 
-    def autotune(self, slices: int = 0, cache: str | None = None) -> int:
-        """Pick the faster radix schedule by timing both (bst_plan_autotune).
-        With a cache path (default: $BST_AUTOTUNE_CACHE if set) the choice is
-        stored per (GPU name, N, V, pad factor) and reused without timing."""
+    def autotune(self, slices: int = 0, cache: str | None = None) -> dict:
+        """Pick the fastest launch shape of the forward path by timing the
+        candidates (bst_plan_autotune: radix schedule, spectrum layout, chunk
+        and block order) and return it (forward_config).  With a cache path
+        (default: $BST_AUTOTUNE_CACHE if set) the choice is stored per (GPU
+        name, N, V, pad factor, gridding) and reused without timing."""
         import json
         import os
         cache = cache or os.environ.get("BST_AUTOTUNE_CACHE")
@@ -139,17 +161,19 @@ class Plan:
                     table = json.load(f)
             except (OSError, ValueError):
                 table = {}
-        if key in table:
-            self.schedule = int(table[key])
-            return self.schedule
+        entry = table.get(key)
+        if isinstance(entry, dict):
+            self.set_forward_config(**entry)
+            return self.forward_config
         chosen = ctypes.c_int(0)
         _check(self._lib.bst_plan_autotune(self._h, int(slices), ctypes.byref(chosen)), "bst_plan_autotune")
+        cfg = self.forward_config
         if cache:
-            table[key] = int(chosen.value)
+            table[key] = cfg
             os.makedirs(os.path.dirname(os.path.abspath(cache)), exist_ok=True)
             with open(cache, "w") as f:
                 json.dump(table, f, indent=1, sort_keys=True)
-        return int(chosen.value)
+        return cfg
 
     # -- forward -------------------------------------------------------------
 

@@ -45,7 +45,11 @@ struct bst_plan_s {
     size_t kb_n = 0;
     int kb_nstrips = 0;
     int chunk_pairs = 1;            // slice pairs per chunk of the forward path
+    int chunk_default = 1;          // the chunk sized to about 64 MiB of workspace
     int maxr = 16;                  // FFT radix schedule of the forward path (16 or 8; autotuned)
+    int fwd_layout = 0;             // BST_LAYOUT_PACKED or BST_LAYOUT_PAIRED (autotuned)
+    int pair_fast = 0;              // gridding blocks ordered pair-fastest (autotuned)
+    int max_lanes = 2;              // streams alternating chunks (1 or 2)
     // two plan-owned streams that alternate chunks of the forward path (fork
     // from and join back to the caller's stream with events), created on first use
     cudaStream_t lane[3] = {nullptr, nullptr, nullptr};
@@ -179,3 +183,6 @@ enum { BSTK_FILTER = 0, BSTK_BACKPROJECT = 1, BSTK_RAW = 2 };
 // flag or-ed into the ray-stage mode: also multiply by the polar cell area
 // |k| (1/4 at k = 0) for KB gridding
 enum { BSTK_KBW = 8 };
+// flag or-ed into the ray-stage mode: write the spectrum in the paired
+// (Z[k], Z[-k]) layout read by the paired bilinear gridding kernel
+enum { BSTK_PAIRED = 16 };

@@ -50,6 +50,26 @@ struct RaySrc {
     }
 };
 
+// Store the weighted spectrum value of bin k of one line.  Packed layout:
+// z[k], k in [0, M).  Paired layout (mode flag BSTK_PAIRED): the line is M/2
+// float4 slots, slot m = (Z[m], Z[-m]) for m in [0, M/2), so that the two
+// taps of a Cartesian point and of its mirror point (which reads bin -k) are
+// one 16-byte load; bin 0 fills both halves of slot 0, the Nyquist bin
+// (weight 0) is not stored.
+__device__ __forceinline__ void spec_store(float2* z, int M, int mode, int k, float2 v) {
+    if (!(mode & BSTK_PAIRED)) {
+        z[k] = v;
+        return;
+    }
+    const int h = M >> 1;
+    if (k < h) {
+        z[2 * k] = v;
+        if (k == 0) z[1] = v;
+    } else if (k > h) {
+        z[2 * (M - k) + 1] = v;
+    }
+}
+
 struct SpecDst {
     float2* z;
     const float* g;
@@ -67,7 +87,7 @@ struct SpecDst {
         else if (md == BSTK_FILTER) w = g ? __ldg(g + ak) : 1.f;
         else w = ak == 0 ? 0.f : __fdiv_rn(two_alpha, (float)ak);
         if (mode & BSTK_KBW) w *= ak == 0 ? 0.25f : (float)ak;
-        z[k] = make_float2(v.x * w, v.y * w);
+        spec_store(z, M, mode, k, make_float2(v.x * w, v.y * w));
     }
 };
 
@@ -327,7 +347,7 @@ struct SpecDstShift {
             const float c = c1 * c2 - s1 * s2, sn = s1 * c2 + c1 * s2;
             v = make_float2(v.x * c - v.y * sn, v.x * sn + v.y * c);
         }
-        z[k] = make_float2(v.x * w, v.y * w);
+        spec_store(z, M, mode, k, make_float2(v.x * w, v.y * w));
     }
 };
 
@@ -426,6 +446,152 @@ __device__ __forceinline__ void grid_unit(float2* smem, int q0, int V, int N, co
         const ColDst<NC> dst{Tp, N, M, side == 0 ? q : (q == 0 ? (M >> 1) : M - q), side == 1 && q != 0, live};
         fft_line_regs<M, TPL, true, MAXR>(t, x, dst, sm, tw);
     }
+}
+
+// Column pairs per block of the paired gridding unit: blocks of at least 256
+// threads (2 TPL threads per column pair).
+template <int M> __host__ __device__ constexpr int paired_cpc() {
+    return (128 / tpl_of<M>()) > 1 ? 128 / tpl_of<M>() : 1;
+}
+
+// P0 + P5 + column P6 for CPC column pairs (q, -q), q = q0 + g, from the
+// paired spectrum layout Z2[V][M/2] (float4 slot (Z[j][k], Z[j][-k]), see
+// spec_store).  A Cartesian point (q, r') and its mirror (-q, -r') share the
+// polar geometry and read the same four slots: at signed radius kappa = +rho
+// the point takes the Z[.][+k] halves and the mirror the Z[.][-k] halves
+// (swapped for kappa = -rho, and again on a seam row, which reads row V-1 or
+// 0 at -k).  The radial taps are always bins floor(rho) and floor(rho) + 1
+// with fraction rho - floor(rho) (the two signed-radius brackets of the
+// packed form give the same value).  2 TPL threads per column pair gather
+// M / (2 TPL) point pairs each into the two shared-memory lines, then
+// threads [0, TPL) of the pair run the inverse FFT of column q and
+// [TPL, 2 TPL) that of column -q (stored index-reversed; column -M/2 pairs
+// with q = 0 and is zero).  PS point pairs per gather step.
+template <int M, int TPL, int CPC, int MAXR, int NC = 0, int PS = 2>
+__device__ __forceinline__ void grid_unit_paired(float2* smem, int q0, int V, int N, const float4* __restrict__ Z2,
+                                                 const int* __restrict__ gJ, const float2* __restrict__ gF,
+                                                 float2* __restrict__ Tp, const float2* __restrict__ tw) {
+    constexpr int H = M >> 1;
+    constexpr int NT = 2 * TPL;
+    constexpr int PPT = M / NT;   // point pairs per thread
+    static_assert(PPT % PS == 0, "point pairs per step");
+    static_assert(NT < 32 || NT % 32 == 0, "groups of 32 or more threads are whole warps");
+    const int g = threadIdx.x / NT;
+    const int lt = threadIdx.x % NT;
+    const int q = q0 + g;
+    const bool live = q < H;
+    const SmemLine l0{smem + 2 * g * smem_line_len(M)};
+    const SmemLine l1{smem + (2 * g + 1) * smem_line_len(M)};
+    const int* gJq = gJ + (size_t)(live ? q : 0) * M;
+    const float2* gFq = gF + (size_t)(live ? q : 0) * M;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    int jn[PS];
+    float2 fn[PS];
+#pragma unroll
+    for (int u = 0; u < PS; ++u) {
+        jn[u] = __ldg(gJq + lt + u * NT);
+        fn[u] = __ldg(gFq + lt + u * NT);
+    }
+#pragma unroll
+    for (int i = 0; i < PPT; i += PS) {
+        int jc[PS];
+        float2 fc[PS];
+#pragma unroll
+        for (int u = 0; u < PS; ++u) {
+            jc[u] = jn[u];
+            fc[u] = fn[u];
+        }
+        if (i + PS < PPT) {
+#pragma unroll
+            for (int u = 0; u < PS; ++u) {
+                jn[u] = __ldg(gJq + lt + (i + PS + u) * NT);
+                fn[u] = __ldg(gFq + lt + (i + PS + u) * NT);
+            }
+        }
+        float4 z[PS][4];
+        bool selA[PS], selB[PS];
+#pragma unroll
+        for (int u = 0; u < PS; ++u) {
+            const int ridx = lt + (i + u) * NT;
+            const int Jt = jc[u] >> 16;
+            const int k0 = jc[u] & 0xffff;
+            // a table bracket >= -1 means the point is inside the band and not the origin
+            const bool ok = live && Jt >= -1;
+            const bool up = signed_freq(ridx, M) >= 0;   // kappa = +rho for the point (q, r'), q >= 0
+            const int J = ok ? Jt : 0;
+            const bool sA = J < 0, sB = J + 1 >= V;
+            const int rowA = sA ? V - 1 : J;
+            const int rowB = sB ? 0 : J + 1;
+            // the point takes the +k halves of a row when up, unless the row is a seam row
+            selA[u] = up != sA;
+            selB[u] = up != sB;
+            const bool k1ok = ok && k0 + 1 < H;
+            const float4* pa = Z2 + (size_t)rowA * H + k0;
+            const float4* pb = Z2 + (size_t)rowB * H + k0;
+            z[u][0] = ok ? __ldg(pa) : zero4;
+            z[u][1] = k1ok ? __ldg(pa + 1) : zero4;
+            z[u][2] = ok ? __ldg(pb) : zero4;
+            z[u][3] = k1ok ? __ldg(pb + 1) : zero4;
+        }
+#pragma unroll
+        for (int u = 0; u < PS; ++u) {
+            const int ridx = lt + (i + u) * NT;
+            const float ft = fc[u].x, fk = fc[u].y;
+            // halves of each slot for the point (p) and its mirror (m)
+            const float4 a0 = z[u][0], a1 = z[u][1], b0 = z[u][2], b1 = z[u][3];
+            const float2 pa0 = selA[u] ? make_float2(a0.x, a0.y) : make_float2(a0.z, a0.w);
+            const float2 ma0 = selA[u] ? make_float2(a0.z, a0.w) : make_float2(a0.x, a0.y);
+            const float2 pa1 = selA[u] ? make_float2(a1.x, a1.y) : make_float2(a1.z, a1.w);
+            const float2 ma1 = selA[u] ? make_float2(a1.z, a1.w) : make_float2(a1.x, a1.y);
+            const float2 pb0 = selB[u] ? make_float2(b0.x, b0.y) : make_float2(b0.z, b0.w);
+            const float2 mb0 = selB[u] ? make_float2(b0.z, b0.w) : make_float2(b0.x, b0.y);
+            const float2 pb1 = selB[u] ? make_float2(b1.x, b1.y) : make_float2(b1.z, b1.w);
+            const float2 mb1 = selB[u] ? make_float2(b1.z, b1.w) : make_float2(b1.x, b1.y);
+            const float2 pA = make_float2(fmaf(fk, pa1.x - pa0.x, pa0.x), fmaf(fk, pa1.y - pa0.y, pa0.y));
+            const float2 pB = make_float2(fmaf(fk, pb1.x - pb0.x, pb0.x), fmaf(fk, pb1.y - pb0.y, pb0.y));
+            const float2 mA = make_float2(fmaf(fk, ma1.x - ma0.x, ma0.x), fmaf(fk, ma1.y - ma0.y, ma0.y));
+            const float2 mB = make_float2(fmaf(fk, mb1.x - mb0.x, mb0.x), fmaf(fk, mb1.y - mb0.y, mb0.y));
+            l0.store(ridx, make_float2(fmaf(ft, pB.x - pA.x, pA.x), fmaf(ft, pB.y - pA.y, pA.y)));
+            l1.store(ridx, q == 0 ? make_float2(0.f, 0.f)
+                                  : make_float2(fmaf(ft, mB.x - mA.x, mA.x), fmaf(ft, mB.y - mA.y, mA.y)));
+        }
+    }
+    // the origin is single-valued: mean over angles of the DC bin (the gather
+    // stored 0 there, from thread 0 of the group, which also writes the mean).
+    // A group of 32 or more threads starts on a warp boundary (NT is then a
+    // multiple of 32), so its first warp reduces with a full-warp shuffle;
+    // smaller groups share a warp with other groups and sum serially.
+    if constexpr (NT >= 32) {
+        if (live && q == 0 && lt < 32) {
+            float sx = 0.f, sy = 0.f;
+            for (int j = lt; j < V; j += 32) {
+                const float4 zz = __ldg(Z2 + (size_t)j * H);
+                sx += zz.x;
+                sy += zz.y;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            }
+            if (lt == 0) l0.store(0, make_float2(sx / (float)V, sy / (float)V));
+        }
+    } else {
+        if (live && q == 0 && lt == 0) {
+            float sx = 0.f, sy = 0.f;
+            for (int j = 0; j < V; ++j) {
+                const float4 zz = __ldg(Z2 + (size_t)j * H);
+                sx += zz.x;
+                sy += zz.y;
+            }
+            l0.store(0, make_float2(sx / (float)V, sy / (float)V));
+        }
+    }
+    __syncthreads();
+    const int half = lt / TPL, t = lt % TPL;
+    const SmemLine& line = half ? l1 : l0;
+    const ColDst<NC> dst{Tp, N, M, half == 0 ? q : (q == 0 ? H : M - q), half == 1 && q != 0, live};
+    fft_line<M, TPL, true, MAXR>(t, line, dst, line, tw);
 }
 
 // row P6 + P7 + P8 for row blocks rb0 .. rb0 + TPC - 1 of four rows (blockDim = 4 TPL TPC);

@@ -9,7 +9,7 @@
 #include <cmath>
 #include <cstdint>
 
-#include "bst_forward.cuh"
+#include "bst_launch.cuh"
 
 namespace bst {
 

@@ -1,6 +1,6 @@
 // fbp_pad2.cu -- the forward-path kernels instantiated for pad factor 2
 // (ray count N = M / 2 as a compile-time constant).
-#include "bst_forward.cuh"
+#include "bst_launch.cuh"
 
 #define BST_FOR_EACH_M(X) \
     X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) X(48) X(96) X(192) X(384) X(768) X(1536) X(3072)

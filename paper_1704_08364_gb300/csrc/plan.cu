@@ -222,6 +222,7 @@ bst_status_t bst_plan_create(bst_plan_t* out, int rays, int angles, const float*
     const size_t per_pair = bsth::fwd_bytes_per_pair(p);
     const size_t budget = (size_t)64 << 20;
     p->chunk_pairs = (int)std::max<size_t>(1, std::min<size_t>(256, budget / per_pair));
+    p->chunk_default = p->chunk_pairs;
     *out = p;
     return BST_OK;
 }
@@ -240,7 +241,7 @@ size_t bst_workspace_bytes(bst_plan_t p, int slices) {
     const int pairs = (slices + 1) / 2;
     const int chunk = std::min(pairs, p->chunk_pairs);
     const int nchunks = (pairs + chunk - 1) / chunk;
-    const int lanes = std::min(nchunks, bsth::kMaxLanes);   // chunks in flight at once
+    const int lanes = std::min(std::min(nchunks, bsth::kMaxLanes), std::max(p->max_lanes, 1));   // chunks in flight
     return (size_t)lanes * chunk * bsth::fwd_bytes_per_pair(p);
 }
 
@@ -335,15 +336,81 @@ bst_status_t bst_plan_set_schedule(bst_plan_t p, int max_radix) {
 
 int bst_plan_get_schedule(bst_plan_t p) { return p ? p->maxr : 0; }
 
+bst_status_t bst_plan_set_forward_config(bst_plan_t p, const bst_fwd_config_t* c) {
+    if (!p || !c) return BST_ERR_INVALID_ARGUMENT;
+    if ((c->max_radix != 8 && c->max_radix != 16) ||
+        (c->layout != BST_LAYOUT_PACKED && c->layout != BST_LAYOUT_PAIRED) || c->chunk_pairs < 1 ||
+        c->chunk_pairs > 256 || (c->pair_fast != 0 && c->pair_fast != 1) || c->max_lanes < 1 ||
+        c->max_lanes > bsth::kMaxLanes)
+        return BST_ERR_INVALID_ARGUMENT;
+    p->maxr = c->max_radix;
+    p->fwd_layout = c->layout;
+    p->chunk_pairs = c->chunk_pairs;
+    p->pair_fast = c->pair_fast;
+    p->max_lanes = c->max_lanes;
+    return BST_OK;
+}
+
+bst_status_t bst_plan_get_forward_config(bst_plan_t p, bst_fwd_config_t* c) {
+    if (!p || !c) return BST_ERR_INVALID_ARGUMENT;
+    c->max_radix = p->maxr;
+    c->layout = p->fwd_layout;
+    c->chunk_pairs = p->chunk_pairs;
+    c->pair_fast = p->pair_fast;
+    c->max_lanes = p->max_lanes;
+    return BST_OK;
+}
+
+// The candidate launch shapes of the autotuner: radix 16 or 8, the packed or
+// (bilinear plans) paired spectrum layout, and the default chunk in
+// column-fastest order or pair-fastest order; where the default chunk is a
+// single pair (the workspace of one pair exceeds L2), also chunks of 2, 4
+// and 8 pairs: the launches then fill more waves of blocks, at the price of a
+// workspace (and intermediates in HBM) that grows with the chunk.  The lane
+// count stays the plan's.
+static std::vector<bst_fwd_config_t> tune_candidates(const bst_plan_s* p) {
+    std::vector<bst_fwd_config_t> out;
+    const int layouts = p->grid_kind == BST_GRID_BILINEAR ? 2 : 1;
+    for (int r : {16, 8})
+        for (int l = 0; l < layouts; ++l) {
+            bst_fwd_config_t c{r, l, p->chunk_default, 0, p->max_lanes};
+            out.push_back(c);
+            if (p->chunk_default == 1) {
+                for (int ch : {2, 4, 8}) {
+                    c.chunk_pairs = ch;
+                    c.pair_fast = 0;
+                    out.push_back(c);
+                    c.pair_fast = 1;
+                    out.push_back(c);
+                }
+            } else {
+                c.pair_fast = 1;
+                out.push_back(c);
+            }
+        }
+    return out;
+}
+
 bst_status_t bst_plan_autotune(bst_plan_t p, int slices, int* chosen) {
     if (!p) return BST_ERR_INVALID_ARGUMENT;
     if (!bsth::on_plan_device(p)) return BST_ERR_INVALID_ARGUMENT;
     if (slices <= 0) {
         const size_t per = (size_t)p->V * p->N * sizeof(float);
-        slices = (int)std::max<size_t>(2, std::min<size_t>(4096, (((size_t)256 << 20) / per) & ~(size_t)1));
+        slices = (int)std::max<size_t>(4, std::min<size_t>(4096, (((size_t)256 << 20) / per) & ~(size_t)1));
     }
+    // at least two chunks of the largest candidate on each lane
+    slices = std::max(slices, p->chunk_default == 1 ? 2 * 2 * 8 * 2 : 4);
+    bst_fwd_config_t old{};
+    bst_plan_get_forward_config(p, &old);
+    const std::vector<bst_fwd_config_t> cand = tune_candidates(p);
+    // workspace for the largest candidate chunk
+    size_t nws = 0;
+    for (const bst_fwd_config_t& c : cand) {
+        bst_plan_set_forward_config(p, &c);
+        nws = std::max(nws, bst_workspace_bytes(p, slices));
+    }
+    bst_plan_set_forward_config(p, &old);
     const size_t nin = (size_t)slices * p->V * p->N, nout = (size_t)slices * p->N * p->N;
-    const size_t nws = bst_workspace_bytes(p, slices);
     float *in = nullptr, *out = nullptr;
     void* ws = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -355,14 +422,12 @@ bst_status_t bst_plan_autotune(bst_plan_t p, int slices, int* chosen) {
     if (st == BST_OK && (cudaMemset(in, 0, nin * sizeof(float)) != cudaSuccess ||
                          cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         st = BST_ERR_CUDA;
-    const int old = p->maxr;
     const bool timing = p->timing;
     p->timing = false;
-    int best = old;
+    bst_fwd_config_t best = old;
     float best_ms = 1e30f;
-    const int cand[2] = {16, 8};
-    for (int c = 0; st == BST_OK && c < 2; ++c) {
-        p->maxr = cand[c];
+    for (size_t c = 0; st == BST_OK && c < cand.size(); ++c) {
+        bst_plan_set_forward_config(p, &cand[c]);
         float ms_min = 1e30f;
         for (int rep = 0; rep < 4 && st == BST_OK; ++rep) {
             cudaEventRecord(e0, nullptr);
@@ -378,7 +443,7 @@ bst_status_t bst_plan_autotune(bst_plan_t p, int slices, int* chosen) {
             best = cand[c];
         }
     }
-    p->maxr = st == BST_OK ? best : old;
+    bst_plan_set_forward_config(p, st == BST_OK ? &best : &old);
     p->timing = timing;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

@@ -83,4 +83,5 @@ def test_both_radix_schedules_match_the_oracle(bst, N):
         got = plan.fbp(torch.from_numpy(sino).cuda()).cpu().numpy()
         assert_parity(got, ref, what=f"schedule {sched} N={N}")
     chosen = plan.autotune(slices=8)
-    assert chosen in (8, 16) and plan.schedule == chosen
+    assert chosen["max_radix"] in (8, 16) and plan.schedule == chosen["max_radix"]
+    assert chosen == plan.forward_config
