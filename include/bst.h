@@ -89,7 +89,9 @@ typedef struct bst_plan_s* bst_plan_t;
 typedef void* bst_stream_t;   /* a cudaStream_t; NULL is the legacy default stream */
 
 /* Create a plan for N = rays detector samples, V = angles projections and pad
- * factor alpha.  angles_rad_host: host array of V float32 angles, copied.
+ * factor alpha (extension; no passage: the paper's problem statement, Sec. 1,
+ * fixes the sizes N and V; the plan holds the tables of stages P3 and P5).
+ * angles_rad_host: host array of V float32 angles, copied.
  * Builds the plan's device tables (twiddles, angle directions, bracket
  * lookup) on the current device.  Errors: INVALID_ARGUMENT (null, V < 2,
  * non-finite, unsorted or out-of-range angles), UNSUPPORTED_SIZE, CUDA,
@@ -101,7 +103,9 @@ bst_status_t bst_plan_create(bst_plan_t* plan, int rays, int angles,
 bst_status_t bst_plan_destroy(bst_plan_t plan);
 
 /* Device workspace in bytes that bst_fbp / bst_backproject need for `slices`
- * slices: the padded polar spectrum Z[chunk][V][M] and the column-transformed
+ * slices (extension; no passage -- the memory budget of Sec. 4 bounds what a
+ * GPU holds at once; here the caller allocates it): the padded polar
+ * spectrum Z[chunk][V][M] and the column-transformed
  * grid T[chunk][N][M] (complex64) for a chunk of slice pairs sized to stay
  * resident in L2 where possible.  0 for an invalid plan or slices <= 0. */
 size_t bst_workspace_bytes(bst_plan_t plan, int slices);
@@ -165,7 +169,9 @@ bst_status_t radon_adjoint(bst_plan_t plan, bst_mode_t mode, const float* d_g,
                            void* d_ws, size_t ws_bytes, bst_stream_t stream);
 
 /* Gradient of sum(grad_vol * FBP(sino; g)) with respect to the M/2 filter
- * taps g (the autograd backward of bst_fbp's d_g):
+ * taps g (the autograd backward of bst_fbp's d_g).  Extension; no passage:
+ * the paper defines the filter weight of stage P4 (Sec. 1's filter F in
+ * BST form), not its gradient, which this library adds for learning taps:
  *   d_grad_g[m] = sum over slices, angles j and |k| = m of
  *                 Re(conj(lambda_j[k]) * Y_j[k]),
  * Y = dt * DFT of the padded rays, lambda = grad_vol pulled back through the
@@ -217,8 +223,11 @@ bst_status_t brute_backproject(bst_plan_t plan, const float* d_sino, int slices,
  * that loads the library until the process exits.  Plans whose one-pair
  * workspace, (V M + 4 ceil(N/4) M) * 8 bytes, exceeds it (for example
  * N = V > 512 at pad factor 2) are rejected with WORKSPACE_TOO_SMALL.
- * The first call on a device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
+ * bst_plan_create looks up the array's device address on the plan's device
+ * (loading the library's device code there, which places the array in
+ * device memory, when the CUDA runtime loads modules lazily), so a call
+ * itself does no set-up and allocates nothing.  cudaDeviceReset ends every
+ * plan of that device; plans created after it refresh the address.
  * All calls on a device share the one array, so calls that overlap on the
  * GPU (different streams or host threads without ordering) race and corrupt
  * each other's results; serialise them.  No scratch content carries over

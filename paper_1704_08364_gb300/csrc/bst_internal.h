@@ -175,6 +175,9 @@ bst_status_t bst_build_geo_table(bst_plan_s* p);
 bst_status_t bst_launch_kb_col(bst_plan_s* p, const float2* Z, float2* T, int np, cudaStream_t st);
 void bst_free_kb(bst_plan_s* p);
 double bst_bessel_i0(double x);
+// look up (and cache) the device address of bst_fbp_noalloc's scratch array
+// on the current device (noalloc.cu); called by bst_plan_create
+bst_status_t bst_noalloc_setup_current_device();
 size_t bst_adjoint_ws(const bst_plan_s* p, int slices);
 size_t bst_brute_ws(const bst_plan_s* p, int slices, int filtered);
 

@@ -10,7 +10,9 @@
 // bst_plan_create, which does allocate its tables) is reused as is.
 //
 // Limit: the scratch array holds BST_NOALLOC_SCRATCH_BYTES = 8 MiB on every
-// GPU that loads the library, for as long as the process lives.  A call is
+// GPU that loads the library, for as long as the process lives.  Its device
+// address is looked up when a plan is created on a device (see
+// bst_noalloc_setup_current_device), so a call does no set-up of its own.  A call is
 // accepted when one slice pair's workspace, (V M + 4 ceil(N/4) M) * 8 bytes,
 // fits in it (for example N = V = 512 at pad factor 2); larger plans are
 // rejected with BST_ERR_WORKSPACE_TOO_SMALL.
@@ -36,23 +38,34 @@ namespace {
 std::mutex g_mu;
 void* g_addr[BST_NOALLOC_MAX_DEVICES] = {nullptr};
 
-// Device address of the scratch array on the current device (set-up on the
-// first call per device, with that device current).
-bst_status_t scratch_address(void** out) {
+// Look up the scratch array's device address on the current device and
+// cache it (refresh = true replaces a cached address).
+bst_status_t resolve(bool refresh, void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return BST_ERR_CUDA;
     if (dev < 0 || dev >= BST_NOALLOC_MAX_DEVICES) return BST_ERR_INVALID_ARGUMENT;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    if (refresh || !g_addr[dev]) {
         void* ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, bst_noalloc_scratch) != cudaSuccess || !ptr) return BST_ERR_CUDA;
+        if (cudaGetSymbolAddress(&ptr, bst_noalloc_scratch) != cudaSuccess || !ptr) {
+            g_addr[dev] = nullptr;
+            return BST_ERR_CUDA;
+        }
         g_addr[dev] = ptr;
     }
-    *out = g_addr[dev];
+    if (out) *out = g_addr[dev];
     return BST_OK;
 }
 
 }  // namespace
+
+// Set-up for the current device, called by bst_plan_create with the plan's
+// device current: the first symbol lookup loads this file's device code on
+// that device (which places the scratch array in device memory), so that it
+// happens when the caller creates a plan, not inside a bst_fbp_noalloc call.
+// A new plan re-reads the address, which keeps it valid after a
+// cudaDeviceReset (which also ends every plan made before it).
+bst_status_t bst_noalloc_setup_current_device() { return resolve(true, nullptr); }
 
 extern "C" {
 
@@ -69,7 +82,7 @@ bst_status_t bst_fbp_noalloc(bst_plan_t p, const float* d_sino, int slices, cons
     const size_t per_pair = bsth::fwd_bytes_per_pair(p);
     if (per_pair > BST_NOALLOC_SCRATCH_BYTES) return BST_ERR_WORKSPACE_TOO_SMALL;
     void* ws = nullptr;
-    const bst_status_t s = scratch_address(&ws);
+    const bst_status_t s = resolve(false, &ws);   // normally cached by bst_plan_create
     if (s != BST_OK) return s;
     // every scratch byte a call reads is written earlier in the same call, so
     // nothing needs clearing between calls

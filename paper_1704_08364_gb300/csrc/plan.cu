@@ -223,6 +223,9 @@ bst_status_t bst_plan_create(bst_plan_t* out, int rays, int angles, const float*
     const size_t budget = (size_t)64 << 20;
     p->chunk_pairs = (int)std::max<size_t>(1, std::min<size_t>(256, budget / per_pair));
     p->chunk_default = p->chunk_pairs;
+    // bst_fbp_noalloc's set-up for this device (a failure here leaves the
+    // plan usable; bst_fbp_noalloc then retries and reports it)
+    if (bst_noalloc_setup_current_device() != BST_OK) cudaGetLastError();
     *out = p;
     return BST_OK;
 }

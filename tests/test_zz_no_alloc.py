@@ -40,8 +40,15 @@ def test_noalloc_matches_fbp_on_two_calls_in_a_row(N, S):
         sino = torch.from_numpy(synth.poisson_log_noise(sino, rng).astype(np.float32)).cuda()
         ref = plan.fbp(sino)
         out = torch.full((S, N, N), float("nan"), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        free_before, _ = torch.cuda.mem_get_info()
         assert _noalloc(lib, plan, sino, out) == 0
         plan.status()
+        free_after, _ = torch.cuda.mem_get_info()
+        # the call itself takes no device memory (its scratch was placed when
+        # the plan was created); the driver's free count is exact on a device
+        # this process uses alone
+        assert free_after == free_before, f"free device memory fell by {free_before - free_after} bytes"
         assert_parity(out.cpu().numpy(), ref.cpu().numpy(), what=f"noalloc N={N} call {call}")
 
 
