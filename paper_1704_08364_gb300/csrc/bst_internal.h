@@ -37,7 +37,7 @@ struct bst_plan_s {
     // sample lists and work items (built by bst_plan_set_gridding)
     int grid_kind = 0;
     int kb_w = 0;
-    float* kb_tab = nullptr;
+    float kb_poly[13] = {0};        // phi as a degree-12 polynomial in t = 2 (2x/W)^2 - 1
     float* kb_dk = nullptr;         // [N]
     int* kb_start = nullptr;        // [kb_nstrips + 1] first work item of each strip
     int* kb_list = nullptr;         // [kb_n] sample ids

@@ -7,7 +7,8 @@
 // at (c_s, r_s) = k (cos theta_j, sin theta_j) bins and is spread onto the W x W
 // Cartesian points c' - c_s, r' - r_s in (-W/2, W/2] with the separable kernel
 // phi(x) = (I0(beta sqrt(1 - (2x/W)^2)) - 1) / (I0(beta) - 1) (the KB kernel
-// without its pedestal, zero at the support edge), on the M-periodic grid.
+// without its pedestal, zero at the support edge), on the M-periodic grid;
+// phi is evaluated as a per-plan polynomial (KbArgs::poly).
 // The division by phi's transform (deapodization) happens in the row stage.
 //
 // One block owns a strip of four consecutive Cartesian columns (storage
@@ -39,40 +40,51 @@
 
 namespace bst {
 
-constexpr int KB_TAB = 8192;   // table intervals over [0, W/2]
+constexpr int KB_POLY = 12;    // degree of the kernel polynomial (see KbArgs::poly)
 constexpr int KB_WMAX = 8;
 constexpr int KB_CS = 4;       // columns per strip
 constexpr int KB_RB = 4;       // rows per band
 constexpr int KB_ITEM = 64;    // entries per work item at most (16 and 128 measured slower)
 
 struct KbArgs {
-    const float* tab;      // [KB_TAB + 2] phi(i W / (2 KB_TAB)); zero from i = KB_TAB on
+    // phi as a polynomial of degree kb_degree(W) <= KB_POLY in
+    // t = 2 (2x/W)^2 - 1 (Chebyshev interpolation of phi at degree + 1 nodes,
+    // built per plan in double precision; monomial coefficients, Horner in
+    // float: absolute error below 3e-7 for every supported width and pad
+    // factor); coefficients above the degree are zero
+    float poly[KB_POLY + 1];
+    float t_scale;         // 8 / W^2, so that t = x^2 t_scale - 1
     const int* istart;     // [nstrips + 1] offsets of the strips' work items
     const int4* items;     // (band, first entry, end entry, 0)
     const int* list;       // sample ids j M + kidx (natural-order bin index)
     const float4* dir;     // [V + 2] (cos_hi, cos_lo, sin_hi, sin_lo) of theta_{j}, at j + 1
     const float* wq;       // [V] angular weights dtheta_j
     int W;                 // kernel width in bins (even, <= KB_WMAX)
-    float tab_scale;       // KB_TAB / (W / 2)
     int nstrips;
 };
 
 template <int M> __host__ __device__ constexpr int kb_threads() { return KB_CS * tpl_of<M>(); }
 
 template <int M> __host__ __device__ constexpr size_t kb_smem_bytes() {
-    return (size_t)KB_CS * smem_line_len(M) * sizeof(float2) + (size_t)(KB_TAB + 2) * sizeof(float);
+    return (size_t)KB_CS * smem_line_len(M) * sizeof(float2);
 }
 
-// phi(|x|) by linear interpolation in the table; zero for |x| >= W/2 (the
-// index saturates on the zero entries; branch-free measured faster than
-// skipping the lookup)
-__device__ __forceinline__ float kb_phi(const float* tab, float x, float scale) {
-    const float u = fabsf(x) * scale;
-    const int i = (int)fminf(u, (float)KB_TAB);
-    const float f = u - (float)i;
-    const float a = tab[i];
-    return fmaf(f, tab[i + 1] - a, a);
+// phi(x): the plan's polynomial of degree DEG in t = 2 (2x/W)^2 - 1 on the
+// support, zero for |x| >= W/2 (t >= 1).  Arithmetic only (the coefficients
+// are kernel arguments), so the weights cost FMA issue instead of
+// shared-memory lookups.  DEG = 10 serves W <= 6 (interpolation error below
+// 1e-7), DEG = 12 all widths (the plan fits the degree it will use).
+template <int DEG = KB_POLY>
+__device__ __forceinline__ float kb_phi(const KbArgs& kb, float x) {
+    const float t = fmaf(x * x, kb.t_scale, -1.f);
+    float h = kb.poly[DEG];
+#pragma unroll
+    for (int i = DEG - 1; i >= 0; --i) h = fmaf(h, t, kb.poly[i]);
+    return t < 1.f ? h : 0.f;
 }
+
+// degree of the kernel polynomial for width W
+__host__ __device__ constexpr int kb_degree(int W) { return W <= 6 ? 10 : KB_POLY; }
 
 // k * (hi + lo) = n + d with n an integer (as float) and |d| <= ~0.5
 __device__ __forceinline__ void kb_split(float k, float hi, float lo, float& n, float& d) {
@@ -91,9 +103,12 @@ __device__ __forceinline__ float kb_dist(int g, float n, float d) {
 }
 
 // accumulate the samples of entries [lo, hi) into the 4 x 4 cell (rows r0..r0+3,
-// columns c0..c0+3) and add the cell to the strip's shared-memory lines
-template <int M>
-__device__ __forceinline__ void kb_item(float2* smem, const float* tab, const KbArgs& kb, const float2* __restrict__ Zp,
+// columns c0..c0+3) and add the cell to the strip's shared-memory lines.  The
+// loads of the next entry (its sample's direction, value and angular weight;
+// the sample id one entry further) are issued before the current entry's
+// arithmetic, so their latency overlaps it.
+template <int M, int DEG>
+__device__ __forceinline__ void kb_item(float2* smem, const KbArgs& kb, const float2* __restrict__ Zp,
                                         int c0, int r0, int lo, int hi) {
     constexpr int LL = smem_line_len(M);
     float ax[KB_CS][KB_RB], ay[KB_CS][KB_RB];
@@ -101,23 +116,47 @@ __device__ __forceinline__ void kb_item(float2* smem, const float* tab, const Kb
     for (int c = 0; c < KB_CS; ++c)
 #pragma unroll
         for (int r = 0; r < KB_RB; ++r) ax[c][r] = ay[c][r] = 0.f;
+    int sn = lo < hi ? __ldg(kb.list + lo) : 0;          // sample id of entry e
+    int sn2 = lo + 1 < hi ? __ldg(kb.list + lo + 1) : 0; // ... of entry e + 1
+    float4 dn = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 zn = make_float2(0.f, 0.f);
+    float wn = 0.f;
+    if (lo < hi) {
+        const int j = sn / M;
+        dn = __ldg(kb.dir + j + 1);
+        zn = __ldg(Zp + sn);
+        wn = __ldg(kb.wq + j);
+    }
     for (int e = lo; e < hi; ++e) {
-        const int s = __ldg(kb.list + e);
+        const int s = sn;
+        const float4 d = dn;
+        const float2 zz = zn;
+        const float wa = wn;
+        if (e + 1 < hi) {
+            sn = sn2;
+            sn2 = e + 2 < hi ? __ldg(kb.list + e + 2) : 0;
+            const int jn = sn / M;
+            dn = __ldg(kb.dir + jn + 1);
+            zn = __ldg(Zp + sn);
+            wn = __ldg(kb.wq + jn);
+        }
         const int j = s / M;
         const int kidx = s - j * M;
         const float k = (float)(kidx < (M >> 1) ? kidx : kidx - M);
-        const float4 d = __ldg(kb.dir + j + 1);
         float nc, dc, nr, dr;
         kb_split(k, d.x, d.y, nc, dc);
         kb_split(k, d.z, d.w, nr, dr);
-        const float2 zz = __ldg(Zp + s);
-        const float wa = __ldg(kb.wq + j);
+        // distances to the band's rows and the strip's columns: the first one
+        // with the periodic wrap, the others one bin further each (a wrap
+        // inside a run of four points only moves points that are at least
+        // M/2 - 4 >= W/2 bins away, where phi is zero either way)
+        const float xr = kb_dist<M>(r0, nr, dr), xc = kb_dist<M>(c0, nc, dc);
         float wr[KB_RB];
 #pragma unroll
-        for (int r = 0; r < KB_RB; ++r) wr[r] = kb_phi(tab, kb_dist<M>(r0 + r, nr, dr), kb.tab_scale);
+        for (int r = 0; r < KB_RB; ++r) wr[r] = kb_phi<DEG>(kb, xr + (float)r);
 #pragma unroll
         for (int c = 0; c < KB_CS; ++c) {
-            const float wc = wa * kb_phi(tab, kb_dist<M>(c0 + c, nc, dc), kb.tab_scale);
+            const float wc = wa * kb_phi<DEG>(kb, xc + (float)c);
             const float zx = wc * zz.x, zy = wc * zz.y;
 #pragma unroll
             for (int r = 0; r < KB_RB; ++r) {
@@ -141,17 +180,17 @@ __device__ __forceinline__ void kb_item(float2* smem, const float* tab, const Kb
 
 // the DC sample at the origin (value z) into the strip's columns
 template <int M>
-__device__ __forceinline__ void kb_spread_dc(float2* smem, const float* tab, const KbArgs& kb, int c0, float2 z) {
+__device__ __forceinline__ void kb_spread_dc(float2* smem, const KbArgs& kb, int c0, float2 z) {
     constexpr int LL = smem_line_len(M);
     const int hw = kb.W >> 1;
     for (int c = 0; c < KB_CS; ++c) {
         const float x = kb_dist<M>(c0 + c, 0.f, 0.f);
         if (fabsf(x) >= (float)hw) continue;
-        const float wc = kb_phi(tab, x, kb.tab_scale);
+        const float wc = kb_phi(kb, x);
         float* line = reinterpret_cast<float*>(smem + c * LL);
         for (int r = -hw + 1; r < hw; ++r) {
             const int rr = r < 0 ? r + M : r;
-            const float w = wc * kb_phi(tab, (float)r, kb.tab_scale);
+            const float w = wc * kb_phi(kb, (float)r);
             const int o = 2 * (rr + (rr >> 4));
             atomicAdd(line + o, w * z.x);
             atomicAdd(line + o + 1, w * z.y);
@@ -167,17 +206,27 @@ __device__ __forceinline__ void kb_col_unit(float2* smem, int strip, int V, int 
                                             const float2* __restrict__ tw) {
     constexpr int NT = KB_CS * TPL;
     constexpr int LL = smem_line_len(M);
-    float* tab = reinterpret_cast<float*>(smem + KB_CS * LL);
+    __shared__ int next_item;
     const int tid = threadIdx.x;
-    for (int i = tid; i < KB_TAB + 2; i += NT) tab[i] = __ldg(kb.tab + i);
     for (int i = tid; i < KB_CS * LL; i += NT) smem[i] = make_float2(0.f, 0.f);
-    __syncthreads();
     const int c0 = strip * KB_CS;
-
     const int i0 = __ldg(kb.istart + strip), i1 = __ldg(kb.istart + strip + 1);
-    for (int i = i0 + tid; i < i1; i += NT) {
-        const int4 it = __ldg(kb.items + i);
-        kb_item<M>(smem, tab, kb, Zp, c0, KB_RB * it.x, it.y, it.z);
+    if (tid == 0) next_item = i0 + NT;
+    __syncthreads();
+
+    // items are ordered longest first; each thread takes the next free one
+    // when it finishes (greedy longest-first), which evens out the threads'
+    // work before the barrier of the column transform
+    if (kb.W <= 6) {
+        for (int i = i0 + tid; i < i1; i = atomicAdd(&next_item, 1)) {
+            const int4 it = __ldg(kb.items + i);
+            kb_item<M, kb_degree(6)>(smem, kb, Zp, c0, KB_RB * it.x, it.y, it.z);
+        }
+    } else {
+        for (int i = i0 + tid; i < i1; i = atomicAdd(&next_item, 1)) {
+            const int4 it = __ldg(kb.items + i);
+            kb_item<M, kb_degree(8)>(smem, kb, Zp, c0, KB_RB * it.x, it.y, it.z);
+        }
     }
 
     // the DC bin of every angle sits at the origin: one weighted sum, spread once
@@ -196,7 +245,7 @@ __device__ __forceinline__ void kb_col_unit(float2* smem, int strip, int V, int 
                     sx += __shfl_xor_sync(0xffffffffu, sx, o);
                     sy += __shfl_xor_sync(0xffffffffu, sy, o);
                 }
-                if (tid == 0) kb_spread_dc<M>(smem, tab, kb, c0, make_float2(sx, sy));
+                if (tid == 0) kb_spread_dc<M>(smem, kb, c0, make_float2(sx, sy));
             }
         } else {
             if (tid == 0) {
@@ -207,7 +256,7 @@ __device__ __forceinline__ void kb_col_unit(float2* smem, int strip, int V, int 
                     sx = fmaf(w, zz.x, sx);
                     sy = fmaf(w, zz.y, sy);
                 }
-                kb_spread_dc<M>(smem, tab, kb, c0, make_float2(sx, sy));
+                kb_spread_dc<M>(smem, kb, c0, make_float2(sx, sy));
             }
         }
     }

@@ -1,4 +1,4 @@
-// kb.cu -- Kaiser-Bessel gridding for stage P5: plan tables (kernel table,
+// kb.cu -- Kaiser-Bessel gridding for stage P5: plan tables (kernel polynomial,
 // deapodization, per-strip sample lists), the gridding + column-FFT kernel
 // and bst_plan_set_gridding.
 //
@@ -43,14 +43,15 @@ bst_status_t launch_kb_col_M(bst_plan_s* p, const float2* Z, float2* T, int np, 
         }))
         return BST_ERR_CUDA;
     KbArgs a;
-    a.tab = p->kb_tab;
+    static_assert(sizeof(a.poly) == sizeof(p->kb_poly), "polynomial size");
+    for (int i = 0; i <= KB_POLY; ++i) a.poly[i] = p->kb_poly[i];
+    a.t_scale = 8.f / (float)(p->kb_w * p->kb_w);
     a.istart = p->kb_start;
     a.items = p->kb_items;
     a.list = p->kb_list;
     a.dir = p->dir;
     a.wq = p->wq;
     a.W = p->kb_w;
-    a.tab_scale = (float)KB_TAB / (float)(p->kb_w / 2);
     a.nstrips = p->kb_nstrips;
     k_kb_col<M, MAXR><<<dim3(p->kb_nstrips, np), kb_threads<M>(), smem, st>>>(Z, p->V, p->N, a, T, p->tw);
     return BST_OK;
@@ -84,12 +85,12 @@ double bst_bessel_i0(double x) {
 }
 
 void bst_free_kb(bst_plan_s* p) {
-    cudaFree(p->kb_tab);
     cudaFree(p->kb_dk);
     cudaFree(p->kb_start);
     cudaFree(p->kb_list);
     cudaFree(p->kb_items);
-    p->kb_tab = p->kb_dk = nullptr;
+    p->kb_dk = nullptr;
+    for (float& c : p->kb_poly) c = 0.f;
     p->kb_start = p->kb_list = nullptr;
     p->kb_items = nullptr;
     p->kb_w = 0;
@@ -104,7 +105,7 @@ static bool upload_vec(T** d, const std::vector<T>& h) {
 }
 
 // Tables of KB gridding of width W for the plan, host-built in double:
-//   the kernel table and the deapodization;
+//   the kernel polynomial and the deapodization;
 //   per strip of four columns, every sample (j, k), k != 0, -M/2, whose
 //   footprint (the W columns c' - c_s in (-W/2, W/2]) meets the strip, sorted
 //   by the first row of its footprint (r' - r_s > -W/2, taken mod M);
@@ -125,13 +126,39 @@ static bst_status_t build_kb(bst_plan_s* p, int W) {
     // without its pedestal, zero at |x| = W/2, so that a footprint edge falling
     // exactly on a grid point adds nothing and the gridded spectrum of a real
     // slice stays Hermitian (the pair packing relies on it)
-    std::vector<float> tab(bst::KB_TAB + 2);
-    for (int i = 0; i <= bst::KB_TAB; ++i) {
-        const double u = (double)i / bst::KB_TAB;   // 2x / W
-        tab[i] = (float)((bst_bessel_i0(beta * std::sqrt(std::max(1.0 - u * u, 0.0))) - 1.0) / (i0b - 1.0));
+    // evaluated on the GPU as a polynomial of degree KB_POLY in t = 2u - 1,
+    // u = (2x/W)^2 in [0, 1] (phi is an entire function of u): interpolation
+    // at the Chebyshev nodes of t, then the Chebyshev series rewritten in
+    // powers of t (all in double; the monomial coefficients stay below 1 in
+    // magnitude, so Horner's rule in float loses only a few ulp)
+    constexpr int DMAX = bst::KB_POLY;
+    const int D = bst::kb_degree(W);
+    double cheb[DMAX + 1] = {0};
+    for (int i = 0; i <= D; ++i) {
+        const double th = M_PI * (i + 0.5) / (D + 1);
+        const double t = std::cos(th);
+        const double u = 0.5 * (t + 1.0);
+        const double f = (bst_bessel_i0(beta * std::sqrt(std::max(1.0 - u, 0.0))) - 1.0) / (i0b - 1.0);
+        for (int k = 0; k <= D; ++k) cheb[k] += f * std::cos(k * th) * (2.0 / (D + 1));
     }
-    tab[bst::KB_TAB] = 0.f;
-    tab[bst::KB_TAB + 1] = 0.f;
+    cheb[0] *= 0.5;
+    double mono[DMAX + 1] = {0}, tk[DMAX + 1] = {0}, tkm1[DMAX + 1] = {0};
+    tkm1[0] = 1.0;                       // T_0
+    tk[1] = 1.0;                         // T_1
+    mono[0] += cheb[0];
+    mono[1] += cheb[1];
+    for (int k = 2; k <= D; ++k) {       // T_k = 2 t T_{k-1} - T_{k-2}
+        double nx[DMAX + 1] = {0};
+        for (int m = 0; m <= D; ++m) {
+            if (m > 0) nx[m] += 2.0 * tk[m - 1];
+            nx[m] -= tkm1[m];
+        }
+        for (int m = 0; m <= D; ++m) {
+            tkm1[m] = tk[m];
+            tk[m] = nx[m];
+            mono[m] += cheb[k] * nx[m];
+        }
+    }
 
     // 1 / C(nu), C(nu) = W (sinh(z) / z - sinc(W nu)) / (I0(beta) - 1),
     // z = sqrt(beta^2 - (pi W nu)^2), sinc(x) = sin(pi x) / (pi x)
@@ -217,13 +244,14 @@ static bst_status_t build_kb(bst_plan_s* p, int W) {
     }
 
     bst_free_kb(p);
-    bool ok = upload_vec(&p->kb_tab, tab) && upload_vec(&p->kb_dk, dk) && upload_vec(&p->kb_start, istart) &&
+    bool ok = upload_vec(&p->kb_dk, dk) && upload_vec(&p->kb_start, istart) &&
               upload_vec(&p->kb_list, list) && upload_vec(&p->kb_items, items);
     if (!ok) {
         cudaGetLastError();
         bst_free_kb(p);
         return BST_ERR_OUT_OF_MEMORY;
     }
+    for (int i = 0; i <= DMAX; ++i) p->kb_poly[i] = i <= D ? (float)mono[i] : 0.f;
     p->kb_w = W;
     p->kb_n = n;
     p->kb_nstrips = ns;
