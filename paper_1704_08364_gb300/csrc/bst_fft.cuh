@@ -148,6 +148,22 @@ __host__ __device__ constexpr int radix_of(int M, int p, int MAXR = 16) {
     return 1 << bits;
 }
 
+// ---- barriers ----------------------------------------------------------------
+
+// Barrier between the passes of a line: the whole block (__syncthreads), or a
+// named barrier shared by the n threads (a multiple of 32) of one worker of a
+// block, so that workers of one block run independent lines.
+struct BlockSync {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct WorkerSync {
+    int id;   // barrier 1..15 (0 is the block's __syncthreads barrier)
+    int n;    // threads of the worker
+    __device__ __forceinline__ void operator()() const {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+    }
+};
+
 // ---- line storage ----------------------------------------------------------
 
 // Shared-memory line with one padding slot per 16 elements (bank-conflict free
@@ -259,9 +275,9 @@ __device__ __forceinline__ void apply_twiddles(const float2* __restrict__ tw, in
     }
 }
 
-template <int M, int R, int NS, int TPL, bool INV, class Src, class Dst>
+template <int M, int R, int NS, int TPL, bool INV, class Src, class Dst, class SYNC>
 __device__ __forceinline__ void stockham_pass(int t, const Src& src, const Dst& dst,
-                                              const float2* __restrict__ tw, bool sync_mid) {
+                                              const float2* __restrict__ tw, bool sync_mid, const SYNC& sync) {
     constexpr int NB = M / R;
     constexpr int IT = (NB + TPL - 1) / TPL;
     float2 a[IT][R];
@@ -282,7 +298,7 @@ __device__ __forceinline__ void stockham_pass(int t, const Src& src, const Dst& 
             }
         }
     }
-    if (sync_mid) __syncthreads();
+    if (sync_mid) sync();
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
         const int j = t + it * TPL;
@@ -314,35 +330,35 @@ __device__ __forceinline__ void stockham_pass(int t, const Src& src, const Dst& 
 
 // Run passes PIDX.. of the length-M transform.  Pass 0 reads `src`, the last
 // pass writes `dst`; the others go through the shared-memory line `sm`.
-// Every thread of the block must call this (it contains __syncthreads()).
-template <int M, int TPL, bool INV, int MAXR, int PIDX, int NS, class Src, class Dst>
+// Every thread that `sync` covers must call this (it contains barriers).
+template <int M, int TPL, bool INV, int MAXR, int PIDX, int NS, class Src, class Dst, class SYNC>
 __device__ __forceinline__ void fft_run(int t, const Src& src, const Dst& dst, const SmemLine& sm,
-                                        const float2* __restrict__ tw) {
+                                        const float2* __restrict__ tw, const SYNC& sync) {
     constexpr int R = radix_of(M, PIDX, MAXR);
     constexpr bool LAST = (NS * R == M);
     if constexpr (PIDX == 0) {
         if constexpr (LAST) {
-            stockham_pass<M, R, NS, TPL, INV>(t, src, dst, tw, Src::kSmem && Dst::kSmem);
+            stockham_pass<M, R, NS, TPL, INV>(t, src, dst, tw, Src::kSmem && Dst::kSmem, sync);
         } else {
-            stockham_pass<M, R, NS, TPL, INV>(t, src, sm, tw, Src::kSmem);
-            __syncthreads();
-            fft_run<M, TPL, INV, MAXR, PIDX + 1, NS * R>(t, src, dst, sm, tw);
+            stockham_pass<M, R, NS, TPL, INV>(t, src, sm, tw, Src::kSmem, sync);
+            sync();
+            fft_run<M, TPL, INV, MAXR, PIDX + 1, NS * R>(t, src, dst, sm, tw, sync);
         }
     } else {
         if constexpr (LAST) {
-            stockham_pass<M, R, NS, TPL, INV>(t, sm, dst, tw, Dst::kSmem);
+            stockham_pass<M, R, NS, TPL, INV>(t, sm, dst, tw, Dst::kSmem, sync);
         } else {
-            stockham_pass<M, R, NS, TPL, INV>(t, sm, sm, tw, true);
-            __syncthreads();
-            fft_run<M, TPL, INV, MAXR, PIDX + 1, NS * R>(t, src, dst, sm, tw);
+            stockham_pass<M, R, NS, TPL, INV>(t, sm, sm, tw, true, sync);
+            sync();
+            fft_run<M, TPL, INV, MAXR, PIDX + 1, NS * R>(t, src, dst, sm, tw, sync);
         }
     }
 }
 
-template <int M, int TPL, bool INV, int MAXR = 16, class Src, class Dst>
+template <int M, int TPL, bool INV, int MAXR = 16, class Src, class Dst, class SYNC = BlockSync>
 __device__ __forceinline__ void fft_line(int t, const Src& src, const Dst& dst, const SmemLine& sm,
-                                         const float2* __restrict__ tw) {
-    fft_run<M, TPL, INV, MAXR, 0, 1>(t, src, dst, sm, tw);
+                                         const float2* __restrict__ tw, const SYNC& sync = SYNC()) {
+    fft_run<M, TPL, INV, MAXR, 0, 1>(t, src, dst, sm, tw, sync);
 }
 
 // The transform of a line whose values thread t already holds in registers,
@@ -352,9 +368,9 @@ __device__ __forceinline__ void fft_line(int t, const Src& src, const Dst& dst, 
 // directly and only its outputs go to the shared-memory line `sm`; the later
 // passes are those of fft_line.  Call with every thread of the block; `sm`
 // must be free for writing (the caller's barrier).
-template <int M, int TPL, bool INV, int MAXR = 16, class Dst>
+template <int M, int TPL, bool INV, int MAXR = 16, class Dst, class SYNC = BlockSync>
 __device__ __forceinline__ void fft_line_regs(int t, float2 (&x)[M / TPL], const Dst& dst, const SmemLine& sm,
-                                              const float2* __restrict__ tw) {
+                                              const float2* __restrict__ tw, const SYNC& sync = SYNC()) {
     constexpr int R = radix_of(M, 0, MAXR);
     constexpr int NB = M / R;
     static_assert(NB % TPL == 0, "one or more whole first-pass butterflies per thread");
@@ -385,8 +401,8 @@ __device__ __forceinline__ void fft_line_regs(int t, float2 (&x)[M / TPL], const
         }
     }
     if constexpr (R < M) {
-        __syncthreads();
-        fft_run<M, TPL, INV, MAXR, 1, R>(t, sm, dst, sm, tw);
+        sync();
+        fft_run<M, TPL, INV, MAXR, 1, R>(t, sm, dst, sm, tw, sync);
     }
 }
 

@@ -226,13 +226,14 @@ __device__ __forceinline__ void gather_side(const float2* __restrict__ Zp, int V
     }
 }
 
+// row r of the kept band of T (layout [ceil(N/4)][M][4])
 struct TileSrc {
     const float2* T;
-    int M, rb, line;
+    int M, r;
     bool live;
     static constexpr bool kSmem = false;
     __device__ __forceinline__ float2 load(int c) const {
-        return live ? __ldg(T + ((size_t)rb * M + c) * 4 + line) : make_float2(0.f, 0.f);
+        return live ? __ldg(T + ((size_t)(r >> 2) * M + c) * 4 + (r & 3)) : make_float2(0.f, 0.f);
     }
 };
 
@@ -369,19 +370,23 @@ __device__ __forceinline__ void ray_unit_prep(float2* smem, int j0, int V, int N
     fft_line<M, TPL, false, MAXR>(t, src, dst, sm, tw);
 }
 
-// P2 + P3 + P4 for lines j0 .. j0 + LPC - 1 of one slice pair (blockDim = TPL * LPC)
-template <int M, int TPL, int LPC, int MAXR, int NC = 0>
+// P2 + P3 + P4 for lines j0 .. j0 + LPC - 1 of one slice pair (TPL * LPC
+// threads; tid the thread's index among them, -1: threadIdx.x; `sync` the
+// barrier that covers them)
+template <int M, int TPL, int LPC, int MAXR, int NC = 0, class SYNC = BlockSync>
 __device__ __forceinline__ void ray_unit(float2* smem, int j0, int V, int N, const float* __restrict__ ya,
                                          const float* __restrict__ yb, int mode, const float* __restrict__ g,
-                                         float two_alpha, float2* __restrict__ Zp, const float2* __restrict__ tw) {
-    const int line = threadIdx.x / TPL, t = threadIdx.x % TPL;
+                                         float two_alpha, float2* __restrict__ Zp, const float2* __restrict__ tw,
+                                         const SYNC& sync = SYNC(), int tid = -1) {
+    if (tid < 0) tid = threadIdx.x;
+    const int line = tid / TPL, t = tid % TPL;
     const int j = j0 + line;
     const bool live = j < V;
     const int jj = live ? j : 0;
     RaySrc<NC> src{ya + (size_t)jj * N, yb ? yb + (size_t)jj * N : nullptr, N, M, live};
     SpecDst dst{Zp + (size_t)jj * M, g, M, mode, two_alpha, live};
     SmemLine sm{smem + line * smem_line_len(M)};
-    fft_line<M, TPL, false, MAXR>(t, src, dst, sm, tw);
+    fft_line<M, TPL, false, MAXR>(t, src, dst, sm, tw, sync);
 }
 
 // P0 + P5 + column P6 for column pairs q0 .. q0 + CPC - 1 (blockDim = TPL * CPC):
@@ -467,17 +472,19 @@ template <int M> __host__ __device__ constexpr int paired_cpc() {
 // threads [0, TPL) of the pair run the inverse FFT of column q and
 // [TPL, 2 TPL) that of column -q (stored index-reversed; column -M/2 pairs
 // with q = 0 and is zero).  PS point pairs per gather step.
-template <int M, int TPL, int CPC, int MAXR, int NC = 0, int PS = 2>
+template <int M, int TPL, int CPC, int MAXR, int NC = 0, int PS = 2, class SYNC = BlockSync>
 __device__ __forceinline__ void grid_unit_paired(float2* smem, int q0, int V, int N, const float4* __restrict__ Z2,
                                                  const int* __restrict__ gJ, const float2* __restrict__ gF,
-                                                 float2* __restrict__ Tp, const float2* __restrict__ tw) {
+                                                 float2* __restrict__ Tp, const float2* __restrict__ tw,
+                                                 const SYNC& sync = SYNC(), int tid = -1) {
     constexpr int H = M >> 1;
     constexpr int NT = 2 * TPL;
     constexpr int PPT = M / NT;   // point pairs per thread
     static_assert(PPT % PS == 0, "point pairs per step");
     static_assert(NT < 32 || NT % 32 == 0, "groups of 32 or more threads are whole warps");
-    const int g = threadIdx.x / NT;
-    const int lt = threadIdx.x % NT;
+    if (tid < 0) tid = threadIdx.x;
+    const int g = tid / NT;
+    const int lt = tid % NT;
     const int q = q0 + g;
     const bool live = q < H;
     const SmemLine l0{smem + 2 * g * smem_line_len(M)};
@@ -587,31 +594,36 @@ __device__ __forceinline__ void grid_unit_paired(float2* smem, int q0, int V, in
             l0.store(0, make_float2(sx / (float)V, sy / (float)V));
         }
     }
-    __syncthreads();
+    sync();
     const int half = lt / TPL, t = lt % TPL;
     const SmemLine& line = half ? l1 : l0;
     const ColDst<NC> dst{Tp, N, M, half == 0 ? q : (q == 0 ? H : M - q), half == 1 && q != 0, live};
-    fft_line<M, TPL, true, MAXR>(t, line, dst, line, tw);
+    fft_line<M, TPL, true, MAXR>(t, line, dst, line, tw, sync);
 }
 
-// row P6 + P7 + P8 for row blocks rb0 .. rb0 + TPC - 1 of four rows (blockDim = 4 TPL TPC);
-// va, vb: the [N][N] images of slices a and b (vb may be null)
-template <int M, int TPL, int TPC, int MAXR, int NC = 0>
+// row P6 + P7 + P8 for row tiles rb0 .. rb0 + TPC - 1 of RPT rows each (RPT TPL
+// TPC threads; tid and sync as for ray_unit): tile b holds rows RPT b ..
+// RPT b + RPT - 1.  RPT = 4 reads T in whole 32-byte groups of four rows; a
+// worker too small for four lines takes RPT = 2.  va, vb: the [N][N] images
+// of slices a and b (vb may be null)
+template <int M, int TPL, int TPC, int MAXR, int NC = 0, class SYNC = BlockSync, int RPT = 4>
 __device__ __forceinline__ void row_unit(float2* smem, int rb0, int N, const float2* __restrict__ Tp,
                                          float* __restrict__ va, float* __restrict__ vb, float scale,
-                                         const float2* __restrict__ tw, const float* __restrict__ dk = nullptr) {
-    const int tile = threadIdx.x / (4 * TPL);
-    const int w = threadIdx.x % (4 * TPL);
-    const int line = w & 3, t = w >> 2;
-    const int rb = rb0 + tile;
-    const int r = rb * 4 + line;
+                                         const float2* __restrict__ tw, const float* __restrict__ dk = nullptr,
+                                         const SYNC& sync = SYNC(), int tid = -1) {
+    static_assert(RPT == 4 || RPT == 2, "rows per tile");
+    if (tid < 0) tid = threadIdx.x;
+    const int tile = tid / (RPT * TPL);
+    const int w = tid % (RPT * TPL);
+    const int line = w % RPT, t = w / RPT;
+    const int r = (rb0 + tile) * RPT + line;
     const bool live = r < N;
     const int rr = live ? r : 0;
-    TileSrc src{Tp, M, live ? rb : 0, line, live};
+    TileSrc src{Tp, M, rr, live};
     VolDst<NC> dst{va + (size_t)rr * N, vb ? vb + (size_t)rr * N : nullptr, N, M,
                dk ? scale * __ldg(dk + rr) : scale, live, dk};
-    SmemLine sm{smem + (tile * 4 + line) * row_line_stride<M>()};
-    fft_line<M, TPL, true, MAXR>(t, src, dst, sm, tw);
+    SmemLine sm{smem + (tile * RPT + line) * row_line_stride<M>()};
+    fft_line<M, TPL, true, MAXR>(t, src, dst, sm, tw, sync);
 }
 
 }  // namespace bst

@@ -3,18 +3,24 @@
 //
 // Items that share a plan are paired (two slices per complex line, as in the
 // per-size path).  Every pair-item is cut into units of the three stages of
-// the forward path (ray FFT, gridding + column inverse FFT, row inverse FFT),
-// each unit filling a 1024-thread block.  One block per SM claims units from
-// a queue in which every unit comes after the units it depends on: stage s
-// of pair-item p is queued at step p + s, so neighbouring items overlap.  A
-// unit of stage 2 or 3 first waits until the previous stage of its item has
-// completed: one thread spins on the item's completion counter with an acquire
-// load and a bounded number of iterations; if the bound is reached it records
-// BST_ERR_TIMEOUT in the batch's error word and the block leaves the loop, so
-// the launch always ends.  The launch is cooperative, which guarantees that all
-// blocks are resident (a unit is only waited on after it has been claimed by a
-// running block).  Each pair-item owns its own workspace region, so no block
-// can hold stale cached lines of data another block writes in the launch.
+// the forward path (ray FFT, gridding + column inverse FFT, row inverse FFT).
+// One 1024-thread block per SM runs two independent 512-thread workers; each
+// worker claims units from a queue in which every unit comes after the units
+// it depends on, and synchronises its threads with its own named barrier, so
+// the two workers of an SM never wait on each other's FFT passes.  A unit
+// fills one worker: for FFT length M (TPL = M/16 or M/12 threads per line)
+// 512 / TPL ray lines, 256 / TPL Cartesian column pairs of the paired
+// spectrum layout (the per-size path's faster gridding kernel), or 512 / TPL
+// rows (tiles of four rows, or of two where four lines exceed the worker).
+// A unit of stage 2 or 3 first waits until the previous stage of its item has
+// completed: the worker's first thread spins on the item's completion counter
+// with an acquire load and a bounded number of iterations; if the bound is
+// reached it records BST_ERR_TIMEOUT in the batch's error word and the worker
+// leaves its loop, so the launch always ends.  The launch is cooperative,
+// which guarantees that all blocks are resident (a unit is only waited on
+// after it has been claimed by a running worker).  Each pair-item owns its own
+// workspace region, so no block can hold stale cached lines of data another
+// block writes in the launch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,7 +38,7 @@ struct RItem {
     float* va;        // slice a volume [N][N]
     float* vb;        // slice b volume or null
     const float* g;   // filter taps [M/2] or null (ramp)
-    float2* Z;        // [V][M]
+    float2* Z;        // [V][M] (paired layout)
     float2* T;        // [ceil(N/4)][M][4]
     const float2* tw;
     const int* gJ;
@@ -43,38 +49,69 @@ struct RItem {
 };
 
 constexpr int RAGGED_THREADS = 1024;
+constexpr int RAGGED_WORKERS = 2;
+constexpr int RAGGED_WT = RAGGED_THREADS / RAGGED_WORKERS;   // threads per worker
 
-template <int M> __host__ __device__ constexpr int r_lines() { return RAGGED_THREADS / tpl_of<M>(); }
+// unit shapes per FFT length
+template <int M> __host__ __device__ constexpr int r_ray_lines() { return RAGGED_WT / tpl_of<M>(); }
+template <int M> __host__ __device__ constexpr int r_grid_pairs() { return RAGGED_WT / (2 * tpl_of<M>()); }
+template <int M> __host__ __device__ constexpr int r_row_rpt() { return 4 * tpl_of<M>() <= RAGGED_WT ? 4 : 2; }
+template <int M> __host__ __device__ constexpr int r_row_tiles() { return RAGGED_WT / (r_row_rpt<M>() * tpl_of<M>()); }
 
-template <int M> __host__ __device__ constexpr size_t r_smem() {
-    return (size_t)(r_lines<M>() * smem_line_len(M) > 4 * (r_lines<M>() / 4) * row_line_stride<M>()
-                        ? r_lines<M>() * smem_line_len(M)
-                        : 4 * (r_lines<M>() / 4) * row_line_stride<M>()) *
-           sizeof(float2);
+// shared memory of one worker (float2 elements): the largest of its units
+template <int M> __host__ __device__ constexpr size_t r_worker_smem() {
+    const size_t a = (size_t)r_ray_lines<M>() * smem_line_len(M);
+    const size_t b = (size_t)2 * r_grid_pairs<M>() * smem_line_len(M);
+    const size_t c = (size_t)r_row_rpt<M>() * r_row_tiles<M>() * row_line_stride<M>();
+    return a > b ? (a > c ? a : c) : (b > c ? b : c);
+}
+
+#define BST_RAGGED_SIZES(X) X(256) X(512) X(768) X(1024) X(1536) X(2048) X(3072) X(4096)
+
+__host__ __device__ constexpr size_t r_max_worker_smem() {
+    size_t m = 0;
+#define BST_SM(mm) m = m > r_worker_smem<mm>() ? m : r_worker_smem<mm>();
+    BST_RAGGED_SIZES(BST_SM)
+#undef BST_SM
+    return m;
 }
 
 // stage units, not inlined, so that every (length, schedule, stage) variant
-// keeps its own register allocation inside the 64-register budget of the kernel
-template <int M, int MAXR>
-__device__ __noinline__ void ray_u(float2* smem, const RItem& it, int u) {
-    constexpr int TPL = tpl_of<M>(), L = r_lines<M>();
-    ray_unit<M, TPL, L, MAXR>(smem, u * L, it.V, it.N, it.sa, it.sb, BSTK_FILTER, it.g, it.two_alpha, it.Z, it.tw);
+// keeps its own register allocation inside the 64-register budget of the
+// kernel (inlining them all spills kilobytes).  NC = M/2 serves items of pad
+// factor 2 (N known at compile time: the first pass skips the zero padding and
+// the last the dropped outputs, as in the per-size kernels); NC = 0 the others.
+template <int M, int MAXR, int NC>
+__device__ __noinline__ void ray_u(float2* smem, const RItem& it, int u, const WorkerSync& sync, int tid) {
+    constexpr int TPL = tpl_of<M>(), L = r_ray_lines<M>();
+    ray_unit<M, TPL, L, MAXR, NC, WorkerSync>(smem, u * L, it.V, it.N, it.sa, it.sb, BSTK_FILTER | BSTK_PAIRED, it.g,
+                                              it.two_alpha, it.Z, it.tw, sync, tid);
+}
+template <int M, int MAXR, int NC>
+__device__ __noinline__ void grid_u(float2* smem, const RItem& it, int u, const WorkerSync& sync, int tid) {
+    constexpr int TPL = tpl_of<M>(), CP = r_grid_pairs<M>();
+    grid_unit_paired<M, TPL, CP, MAXR, NC, 2, WorkerSync>(smem, u * CP, it.V, it.N,
+                                                          reinterpret_cast<const float4*>(it.Z), it.gJ, it.gF, it.T,
+                                                          it.tw, sync, tid);
+}
+template <int M, int MAXR, int NC>
+__device__ __noinline__ void row_u(float2* smem, const RItem& it, int u, const WorkerSync& sync, int tid) {
+    constexpr int TPL = tpl_of<M>(), TT = r_row_tiles<M>(), RPT = r_row_rpt<M>();
+    row_unit<M, TPL, TT, MAXR, NC, WorkerSync, RPT>(smem, u * TT, it.N, it.T, it.va, it.vb, it.scale, it.tw,
+                                                    nullptr, sync, tid);
+}
+template <int M, int MAXR, int NC>
+__device__ __forceinline__ void run_unit_nc(float2* smem, const RItem& it, int stage, int u, const WorkerSync& sync,
+                                            int tid) {
+    if (stage == 0) ray_u<M, MAXR, NC>(smem, it, u, sync, tid);
+    else if (stage == 1) grid_u<M, MAXR, NC>(smem, it, u, sync, tid);
+    else row_u<M, MAXR, NC>(smem, it, u, sync, tid);
 }
 template <int M, int MAXR>
-__device__ __noinline__ void grid_u(float2* smem, const RItem& it, int u) {
-    constexpr int TPL = tpl_of<M>(), L = r_lines<M>();
-    grid_unit<M, TPL, L, MAXR>(smem, u * L, it.V, it.N, it.Z, it.gJ, it.gF, it.T, it.tw);
-}
-template <int M, int MAXR>
-__device__ __noinline__ void row_u(float2* smem, const RItem& it, int u) {
-    constexpr int TPL = tpl_of<M>(), L = r_lines<M>();
-    row_unit<M, TPL, L / 4, MAXR>(smem, u * (L / 4), it.N, it.T, it.va, it.vb, it.scale, it.tw);
-}
-template <int M, int MAXR>
-__device__ __forceinline__ void run_unit(float2* smem, const RItem& it, int stage, int u) {
-    if (stage == 0) ray_u<M, MAXR>(smem, it, u);
-    else if (stage == 1) grid_u<M, MAXR>(smem, it, u);
-    else row_u<M, MAXR>(smem, it, u);
+__device__ __forceinline__ void run_unit(float2* smem, const RItem& it, int stage, int u, const WorkerSync& sync,
+                                         int tid) {
+    if (2 * it.N == M) run_unit_nc<M, MAXR, M / 2>(smem, it, stage, u, sync, tid);
+    else run_unit_nc<M, MAXR, 0>(smem, it, stage, u, sync, tid);
 }
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -83,23 +120,30 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
     return v;
 }
 
-#define BST_RAGGED_SIZES(X) X(256) X(512) X(768) X(1024) X(1536) X(2048) X(3072) X(4096)
-
 __global__ void __launch_bounds__(RAGGED_THREADS, 1)
     k_ragged(const RItem* __restrict__ items, const int4* __restrict__ queue, int nq, int* __restrict__ next,
              int* __restrict__ done, int* __restrict__ err, int spin_limit) {
     extern __shared__ float2 smem[];
-    __shared__ int s_u, s_ok;
+    __shared__ int s_u[RAGGED_WORKERS], s_ok[RAGGED_WORKERS];
+    const int wk = threadIdx.x / RAGGED_WT;
+    const int tid = threadIdx.x % RAGGED_WT;
+    const WorkerSync sync{1 + wk, RAGGED_WT};
+    float2* wsm = smem + (size_t)wk * r_max_worker_smem();
+    int claimed = -1;   // thread 0: the entry claimed ahead of time
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_u = atomicAdd(next, 1);
-        __syncthreads();
-        const int u = s_u;
+        sync();   // the worker's previous entry is done with its shared memory and s_u
+        if (tid == 0) s_u[wk] = claimed >= 0 ? claimed : atomicAdd(next, 1);
+        sync();
+        const int u = s_u[wk];
         if (u >= nq) break;
-        const int4 w = queue[u];   // (pair-item, stage, unit)
+        // claim the next entry now, so that the atomic's latency overlaps this
+        // entry's work (claims stay in queue order per worker: the oldest
+        // claimed, unfinished entry is always some worker's current one)
+        if (tid == 0) claimed = atomicAdd(next, 1);
+        const int4 w = queue[u];   // (pair-item, stage, first unit, units)
         const RItem& it = items[w.x];
         if (w.y > 0) {
-            if (threadIdx.x == 0) {
+            if (tid == 0) {
                 const int need = it.n[w.y - 1];
                 const int* c = done + 3 * w.x + (w.y - 1);
                 int ok = 1, n = 0;
@@ -111,38 +155,36 @@ __global__ void __launch_bounds__(RAGGED_THREADS, 1)
                     }
                     __nanosleep(256);
                 }
-                s_ok = ok;
+                s_ok[wk] = ok;
             }
-            __syncthreads();
-            if (!s_ok) break;
+            sync();
+            if (!s_ok[wk]) break;
         }
-        switch (it.M) {
-#define BST_UNIT(m)                                         \
-    case m:                                                 \
-        if (it.maxr == 8) run_unit<m, 8>(smem, it, w.y, w.z); \
-        else run_unit<m, 16>(smem, it, w.y, w.z);           \
+        for (int k = 0; k < w.w; ++k) {
+            if (k > 0) sync();   // the previous unit is done with the shared memory
+            switch (it.M) {
+#define BST_UNIT(m)                                                                \
+    case m:                                                                        \
+        if (it.maxr == 8) run_unit<m, 8>(wsm, it, w.y, w.z + k, sync, tid);        \
+        else run_unit<m, 16>(wsm, it, w.y, w.z + k, sync, tid);                    \
         break;
-            BST_RAGGED_SIZES(BST_UNIT)
+                BST_RAGGED_SIZES(BST_UNIT)
 #undef BST_UNIT
-            default:
-                break;
+                default:
+                    break;
+            }
         }
-        __syncthreads();
-        if (threadIdx.x == 0 && w.y < 2) {
-            // release: the block's writes of this unit (ordered before by the
+        sync();
+        if (tid == 0 && w.y < 2) {
+            // release: the worker's writes of these units (ordered before by its
             // barrier) become visible to a unit that acquires the counter
-            asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(done + 3 * w.x + w.y) : "memory");
+            asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(done + 3 * w.x + w.y), "r"(w.w)
+                         : "memory");
         }
     }
 }
 
-__host__ size_t ragged_smem_bytes() {
-    size_t m = 0;
-#define BST_SM(mm) m = std::max(m, r_smem<mm>());
-    BST_RAGGED_SIZES(BST_SM)
-#undef BST_SM
-    return m;
-}
+__host__ size_t ragged_smem_bytes() { return (size_t)RAGGED_WORKERS * r_max_worker_smem() * sizeof(float2); }
 
 __host__ bool ragged_supported(int M) {
     switch (M) {
@@ -153,7 +195,16 @@ __host__ bool ragged_supported(int M) {
     return false;
 }
 
-__host__ int ragged_lines(int M) { return RAGGED_THREADS / ((M % 3 == 0) ? M / 12 : M / 16); }
+// units per stage of an item of FFT length M, N rays and V angles
+__host__ void ragged_units(int M, int N, int V, int* n) {
+    const int tpl = (M % 3 == 0) ? M / 12 : M / 16;
+    const int lines = RAGGED_WT / tpl;                  // ray lines per unit
+    const int pairs = RAGGED_WT / (2 * tpl);            // column pairs per unit
+    const int rows = RAGGED_WT / tpl;                   // rows per unit (tiles x rows per tile)
+    n[0] = (V + lines - 1) / lines;
+    n[1] = (M / 2 + pairs - 1) / pairs;
+    n[2] = (N + rows - 1) / rows;
+}
 
 }  // namespace bst
 
@@ -315,17 +366,25 @@ bst_status_t bst_ragged_bind(bst_ragged_t r, const float* const* d_sinos, const 
         x.maxr = p->maxr;
         x.scale = (float)((double)p->N / (2.0 * (double)p->M * (double)p->M));
         x.two_alpha = (float)(2 * p->alpha);
-        const int L = bst::ragged_lines(p->M);
-        x.n[0] = (p->V + L - 1) / L;
-        x.n[1] = (p->M / 2 + L - 1) / L;
-        x.n[2] = ((p->N + 3) / 4 + L / 4 - 1) / (L / 4);
+        bst::ragged_units(p->M, p->N, p->V, x.n);
     }
-    // queue; a unit always follows its dependencies.  Default: phases (every
-    // ray unit, then every gridding unit, then every row unit), the largest
-    // pair-items first within a phase (measured 6 % faster on a 64-item batch).
-    // Flag bit 1: stage s of pair-item k at step k + s (neighbouring items overlap).
+    // queue of entries (pair-item, stage, first unit, units), each entry a run
+    // of up to RAGGED_RUN units of one stage (every unit is 8192 points of FFT
+    // work whatever the length, so entries are of about equal size); an entry
+    // always follows the entries it depends on.  Default: phases (every ray
+    // entry, then every gridding entry, then every row entry), the largest
+    // pair-items first within a phase.  Flag bit 1: stage s of pair-item k at
+    // step k + s (neighbouring items overlap).
+    // (runs of RAGGED_RUN units for lengths of 2048 and more, whose items have
+    // units enough to fill every worker; single units for the others)
+    constexpr int RAGGED_RUN = 4;
     std::vector<int4> q;
     const bool skip0 = (flags & 1) != 0;   // diagnostic: leave pair-item 0's ray stage unqueued
+    auto push_stage = [&](int k, int s) {
+        if (s == 0 && k == 0 && skip0) return;
+        const int run = it[k].M >= 2048 ? RAGGED_RUN : 1;
+        for (int u = 0; u < it[k].n[s]; u += run) q.push_back(make_int4(k, s, u, std::min(run, it[k].n[s] - u)));
+    };
     if (!(flags & 2)) {
         std::vector<int> order(pairs);
         for (int k = 0; k < pairs; ++k) order[k] = k;
@@ -333,17 +392,12 @@ bst_status_t bst_ragged_bind(bst_ragged_t r, const float* const* d_sinos, const 
             return (size_t)it[a].M * it[a].V > (size_t)it[b].M * it[b].V;
         });
         for (int s = 0; s < 3; ++s)
-            for (int k : order) {
-                if (s == 0 && k == 0 && skip0) continue;
-                for (int u = 0; u < it[k].n[s]; ++u) q.push_back(make_int4(k, s, u, 0));
-            }
+            for (int k : order) push_stage(k, s);
     } else {
         for (int step = 0; step < pairs + 2; ++step)
             for (int s = 0; s < 3; ++s) {
                 const int k = step - s;
-                if (k < 0 || k >= pairs) continue;
-                if (s == 0 && k == 0 && skip0) continue;
-                for (int u = 0; u < it[k].n[s]; ++u) q.push_back(make_int4(k, s, u, 0));
+                if (k >= 0 && k < pairs) push_stage(k, s);
             }
     }
     int4* dq = nullptr;
