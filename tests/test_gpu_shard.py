@@ -64,3 +64,15 @@ def test_virtual_ranks_filter_gradient_sums_to_full_batch(bst):
     scale = full.abs().max().item()
     assert scale > 0
     np.testing.assert_allclose(total.cpu().numpy(), full.cpu().numpy(), rtol=0, atol=2e-5 * scale)
+
+
+def test_device_generator_slices_equal_those_of_the_whole_volume():
+    """bench.py --scaling strong generates each rank's slice range on its own
+    device (first_slice): ellipses and noise must equal those slices of the
+    whole volume generated at once, so every rank reconstructs its share of
+    one workload."""
+    from synth import device as sdev
+    whole = sdev.ellipse_volume(2, 8, 64, 96, noise_frac=0.01, device="cuda")
+    for s0, s1 in ((0, 4), (4, 8), (2, 6)):
+        part = sdev.ellipse_volume(2, s1 - s0, 64, 96, noise_frac=0.01, device="cuda", first_slice=s0)
+        assert torch.equal(part, whole[s0:s1]), (s0, s1)
