@@ -105,7 +105,13 @@ STAGE_NAMES = {0: "k_ray_fft", 1: "k_grid_col", 2: "k_row_ifft", 3: "k_ss_filter
 # reports traffic null.
 KERNEL_SOURCES = ["paper_1704_08364_gb300/csrc/bst_forward.cuh", "paper_1704_08364_gb300/csrc/bst_stages.cuh",
                   "paper_1704_08364_gb300/csrc/bst_fft.cuh", "paper_1704_08364_gb300/csrc/bst_geo.cuh"]
-CAPTURED_TRAFFIC = []
+CAPTURED_TRAFFIC = [
+    {"sha": "2b3f36f2de79e2136ed6602effb3ad0d32a49e07292d43605458d51bbc832687",
+     "rays": 2048, "pad": 2,
+     "shape": {"layout": "paired", "chunk_pairs": 8, "pair_fast": 1, "max_radix": 16},
+     "bytes": {"k_ray_fft": 269732096 + 475529216, "k_grid_col": 630232832 + 489338368,
+               "k_row_ifft": 536913920 + 237172224}},
+]
 
 
 def device_code_sha() -> str:
