@@ -50,28 +50,41 @@ struct RaySrc {
     }
 };
 
-// Store the weighted spectrum value of bin k of one line.  Packed layout:
-// z[k], k in [0, M).  Paired layout (mode flag BSTK_PAIRED): the line is M/2
-// float4 slots, slot m = (Z[m], Z[-m]) for m in [0, M/2), so that the two
-// taps of a Cartesian point and of its mirror point (which reads bin -k) are
-// one 16-byte load; bin 0 fills both halves of slot 0, the Nyquist bin
-// (weight 0) is not stored.
-__device__ __forceinline__ void spec_store(float2* z, int M, int mode, int k, float2 v) {
+// Slot of bin m of row j in the paired layout of one pair's spectrum (V rows
+// of M/2 slots of 16 bytes, slot (Z[j][m], Z[j][-m])): rows are stored two by
+// two, each 128-byte line holding bins 4i .. 4i + 3 of rows 2p and 2p + 1, so
+// the two rows of a bilinear bracket often share a line and the taps of a
+// warp fall on about a fifth fewer lines than with whole rows; with V odd the
+// last row is stored whole after the pairs.
+__host__ __device__ __forceinline__ int paired_slot(int j, int m, int H, int V) {
+    const int ve = V & ~1;
+    return j < ve ? ((((j >> 1) * (H >> 2)) + (m >> 2)) << 3) + ((j & 1) << 2) + (m & 3) : ve * H + m;
+}
+
+// Store the weighted spectrum value of bin k of row j of one pair's spectrum
+// z (the pair's base).  Packed layout: z[j M + k], k in [0, M).  Paired
+// layout (mode flag BSTK_PAIRED): slot m of row j holds (Z[m], Z[-m]) for
+// m in [0, M/2), placed by paired_slot, so that the two taps of a Cartesian
+// point and of its mirror point (which reads bin -k) are one 16-byte load;
+// bin 0 fills both halves of slot 0, the Nyquist bin (weight 0) is not stored.
+__device__ __forceinline__ void spec_store(float2* z, int j, int V, int M, int mode, int k, float2 v) {
     if (!(mode & BSTK_PAIRED)) {
-        z[k] = v;
+        z[(size_t)j * M + k] = v;
         return;
     }
     const int h = M >> 1;
     if (k < h) {
-        z[2 * k] = v;
-        if (k == 0) z[1] = v;
+        const int s = paired_slot(j, k, h, V);
+        z[2 * s] = v;
+        if (k == 0) z[2 * s + 1] = v;
     } else if (k > h) {
-        z[2 * (M - k) + 1] = v;
+        z[2 * paired_slot(j, M - k, h, V) + 1] = v;
     }
 }
 
 struct SpecDst {
-    float2* z;
+    float2* z;      // the pair's spectrum
+    int j, V;       // row (angle) of this line, rows of the pair
     const float* g;
     int M, mode;
     float two_alpha;
@@ -87,7 +100,7 @@ struct SpecDst {
         else if (md == BSTK_FILTER) w = g ? __ldg(g + ak) : 1.f;
         else w = ak == 0 ? 0.f : __fdiv_rn(two_alpha, (float)ak);
         if (mode & BSTK_KBW) w *= ak == 0 ? 0.25f : (float)ak;
-        spec_store(z, M, mode, k, make_float2(v.x * w, v.y * w));
+        spec_store(z, j, V, M, mode, k, make_float2(v.x * w, v.y * w));
     }
 };
 
@@ -321,7 +334,8 @@ struct RaySrcPrep {
 };
 
 struct SpecDstShift {
-    float2* z;
+    float2* z;      // the pair's spectrum
+    int j, V;       // row (angle) of this line, rows of the pair
     const float* g;
     int M, mode;
     float two_alpha;
@@ -348,7 +362,7 @@ struct SpecDstShift {
             const float c = c1 * c2 - s1 * s2, sn = s1 * c2 + c1 * s2;
             v = make_float2(v.x * c - v.y * sn, v.x * sn + v.y * c);
         }
-        spec_store(z, M, mode, k, make_float2(v.x * w, v.y * w));
+        spec_store(z, j, V, M, mode, k, make_float2(v.x * w, v.y * w));
     }
 };
 
@@ -365,7 +379,7 @@ __device__ __forceinline__ void ray_unit_prep(float2* smem, int j0, int V, int N
     const bool live = j < V;
     const int jj = live ? j : 0;
     RaySrcPrep<NC> src{ya + (size_t)jj * N, yb ? yb + (size_t)jj * N : nullptr, da, db, fa, fb, N, M, live, pa};
-    SpecDstShift dst{Zp + (size_t)jj * M, g, M, mode, two_alpha, live, pa};
+    SpecDstShift dst{Zp, jj, V, g, M, mode, two_alpha, live, pa};
     SmemLine sm{smem + line * smem_line_len(M)};
     fft_line<M, TPL, false, MAXR>(t, src, dst, sm, tw);
 }
@@ -384,7 +398,7 @@ __device__ __forceinline__ void ray_unit(float2* smem, int j0, int V, int N, con
     const bool live = j < V;
     const int jj = live ? j : 0;
     RaySrc<NC> src{ya + (size_t)jj * N, yb ? yb + (size_t)jj * N : nullptr, N, M, live};
-    SpecDst dst{Zp + (size_t)jj * M, g, M, mode, two_alpha, live};
+    SpecDst dst{Zp, jj, V, g, M, mode, two_alpha, live};
     SmemLine sm{smem + line * smem_line_len(M)};
     fft_line<M, TPL, false, MAXR>(t, src, dst, sm, tw, sync);
 }
@@ -533,12 +547,11 @@ __device__ __forceinline__ void grid_unit_paired(float2* smem, int q0, int V, in
             selA[u] = up != sA;
             selB[u] = up != sB;
             const bool k1ok = ok && k0 + 1 < H;
-            const float4* pa = Z2 + (size_t)rowA * H + k0;
-            const float4* pb = Z2 + (size_t)rowB * H + k0;
-            z[u][0] = ok ? __ldg(pa) : zero4;
-            z[u][1] = k1ok ? __ldg(pa + 1) : zero4;
-            z[u][2] = ok ? __ldg(pb) : zero4;
-            z[u][3] = k1ok ? __ldg(pb + 1) : zero4;
+            const int k1 = k1ok ? k0 + 1 : k0;
+            z[u][0] = ok ? __ldg(Z2 + paired_slot(rowA, k0, H, V)) : zero4;
+            z[u][1] = k1ok ? __ldg(Z2 + paired_slot(rowA, k1, H, V)) : zero4;
+            z[u][2] = ok ? __ldg(Z2 + paired_slot(rowB, k0, H, V)) : zero4;
+            z[u][3] = k1ok ? __ldg(Z2 + paired_slot(rowB, k1, H, V)) : zero4;
         }
 #pragma unroll
         for (int u = 0; u < PS; ++u) {
@@ -572,7 +585,7 @@ __device__ __forceinline__ void grid_unit_paired(float2* smem, int q0, int V, in
         if (live && q == 0 && lt < 32) {
             float sx = 0.f, sy = 0.f;
             for (int j = lt; j < V; j += 32) {
-                const float4 zz = __ldg(Z2 + (size_t)j * H);
+                const float4 zz = __ldg(Z2 + paired_slot(j, 0, H, V));
                 sx += zz.x;
                 sy += zz.y;
             }
@@ -587,7 +600,7 @@ __device__ __forceinline__ void grid_unit_paired(float2* smem, int q0, int V, in
         if (live && q == 0 && lt == 0) {
             float sx = 0.f, sy = 0.f;
             for (int j = 0; j < V; ++j) {
-                const float4 zz = __ldg(Z2 + (size_t)j * H);
+                const float4 zz = __ldg(Z2 + paired_slot(j, 0, H, V));
                 sx += zz.x;
                 sy += zz.y;
             }

@@ -32,12 +32,14 @@ def _oracle(sino, theta, alpha, mode):
     return np.stack([ob.bst(s.astype(np.float64), theta, alpha, m) for s in sino])
 
 
-@pytest.mark.parametrize("N,V,alpha", [(8, 8, 2), (24, 20, 2), (32, 32, 1), (48, 40, 2), (96, 70, 1),
-                                       (128, 100, 2), (192, 128, 2), (256, 256, 1), (384, 300, 2),
+@pytest.mark.parametrize("N,V,alpha", [(8, 8, 2), (24, 21, 2), (32, 32, 1), (48, 40, 2), (64, 37, 1), (96, 70, 1),
+                                       (128, 100, 2), (192, 127, 2), (256, 256, 1), (384, 300, 2),
                                        (512, 96, 2)])
 def test_every_launch_shape_matches_the_oracle(bst, N, V, alpha):
-    """Both FFT-length families (2^a, 3 * 2^a), both pad factors, 7 slices (an
-    odd count: the last pair is padded; chunks that do not divide the pairs)."""
+    """Both FFT-length families (2^a, 3 * 2^a), both pad factors, odd and even
+    angle counts (the paired layout stores rows two by two; an odd last row
+    whole), 7 slices (an odd count: the last pair is padded; chunks that do not
+    divide the pairs)."""
     rng = np.random.default_rng(7 * N + V)
     theta = synth.uniform_angles(V)
     S = 7

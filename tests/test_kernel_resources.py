@@ -51,3 +51,18 @@ def test_gridding_kernels_keep_their_blocks_per_sm(report):
         regs, spill = report[name]
         assert regs <= 64, f"{name} uses {regs} registers"
         assert spill <= 32, f"{name} spills {spill} bytes"
+
+
+def test_paired_layout_slot_map_is_a_bijection(tmp_path):
+    """The paired spectrum layout's slot map (paired_slot in bst_stages.cuh)
+    covers the pair's workspace exactly once, with odd and even row counts."""
+    nvcc = NVCC if os.path.exists(NVCC) else shutil.which("nvcc")
+    if not nvcc:
+        pytest.skip("nvcc not available")
+    exe = tmp_path / "layout_check"
+    r = subprocess.run([nvcc, "-std=c++17", "-O2", "-I", os.path.join(ROOT, "paper_1704_08364_gb300", "csrc"),
+                        "-I", os.path.join(ROOT, "include"), "-x", "cu", os.path.join(ROOT, "tests", "layout_check.cu"),
+                        "-o", str(exe)], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and out.stdout.strip() == "OK", out.stdout + out.stderr
