@@ -40,20 +40,21 @@ namespace bst {
 // ---------------------------------------------------------------------------
 // per-size kernels: one slice pair per blockIdx.y of a chunk
 
-template <int M, int TPL, int LPC, int MAXR, int NC = 0>
-__global__ void __launch_bounds__(TPL * LPC)
+// ILV: the block's LPC angle rows interleaved over its lanes (ray_unit)
+template <int M, int TPL, int LPC, int MAXR, int NC = 0, bool ILV = false>
+__global__ void __launch_bounds__(TPL * LPC, (TPL * LPC <= 1024) ? 1024 / (TPL * LPC) : 1)
     k_ray_fft(const float* __restrict__ sino, int slices, int pair0, int N, int V, int mode,
               const float* __restrict__ g, float two_alpha, float2* __restrict__ Z, const float2* __restrict__ tw) {
     extern __shared__ float2 smem[];
     const int pl = blockIdx.y;
     const int sa = 2 * (pair0 + pl), sb = sa + 1;
-    ray_unit<M, TPL, LPC, MAXR, NC>(smem, blockIdx.x * LPC, V, N, sino + (size_t)sa * V * N,
-                                sb < slices ? sino + (size_t)sb * V * N : nullptr, mode, g, two_alpha,
-                                Z + (size_t)pl * V * M, tw);
+    ray_unit<M, TPL, LPC, MAXR, NC, BlockSync, ILV>(smem, blockIdx.x * LPC, V, N, sino + (size_t)sa * V * N,
+                                                    sb < slices ? sino + (size_t)sb * V * N : nullptr, mode, g,
+                                                    two_alpha, Z + (size_t)pl * V * M, tw);
 }
 
 template <int M, int TPL, int LPC, int MAXR, int NC = 0>
-__global__ void __launch_bounds__(TPL * LPC)
+__global__ void __launch_bounds__(TPL * LPC, (TPL * LPC <= 1024) ? 1024 / (TPL * LPC) : 1)
     k_ray_fft_prep(const float* __restrict__ sino, int slices, int pair0, int N, int V, PrepArgs pa, int mode,
                    const float* __restrict__ g, float two_alpha, float2* __restrict__ Z,
                    const float2* __restrict__ tw) {

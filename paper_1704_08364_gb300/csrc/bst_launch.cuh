@@ -23,10 +23,14 @@ static bool set_smem(K kernel, size_t bytes) {
 
 template <int M> struct FwdCfg {
     static constexpr int TPL = tpl_of<M>();
-    static constexpr int LPC1 = (256 / TPL) > 1 ? 256 / TPL : 1;
+    // ray kernel: 256 threads a block, or, for lengths whose line takes 256
+    // threads, two interleaved angle rows in 512 (whole lines of the paired
+    // layout per warp store)
+    static constexpr bool ILV1 = TPL >= 256;
+    static constexpr int LPC1 = ILV1 ? 2 : ((256 / TPL) > 1 ? 256 / TPL : 1);
     static constexpr int CPC = (128 / TPL) > 1 ? 128 / TPL : 1;
     static constexpr int TPC = (128 / (4 * TPL)) > 1 ? 128 / (4 * TPL) : 1;
-    static constexpr size_t S1 = (size_t)LPC1 * smem_line_len(M) * sizeof(float2);
+    static constexpr size_t S1 = (size_t)LPC1 * ray_line_stride<M, ILV1>() * sizeof(float2);
     static constexpr size_t S2 = (size_t)CPC * smem_line_len(M) * sizeof(float2);
     static constexpr int CPCP = paired_cpc<M>();
     static constexpr size_t S2P = (size_t)2 * CPCP * smem_line_len(M) * sizeof(float2);
@@ -39,7 +43,7 @@ bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int 
     using C = FwdCfg<M>;
     static std::atomic<unsigned long long> attr_done{0};
     if (!bsth::once_per_device(attr_done, [] {
-            return set_smem(k_ray_fft<M, C::TPL, C::LPC1, MAXR, NC>, C::S1) &&
+            return set_smem(k_ray_fft<M, C::TPL, C::LPC1, MAXR, NC, C::ILV1>, C::S1) &&
                    set_smem(k_ray_fft_prep<M, C::TPL, C::LPC1, MAXR, NC>, C::S1) &&
                    set_smem(k_grid_col<M, C::TPL, C::CPC, MAXR, NC>, C::S2) &&
                    set_smem(k_grid_col_paired<M, C::TPL, C::CPCP, MAXR, NC>, C::S2P) &&
@@ -84,7 +88,7 @@ bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int 
                 <<<dim3((V + C::LPC1 - 1) / C::LPC1, np), C::TPL * C::LPC1, C::S1, s>>>(
                     sino, slices, p0, N, V, *prep, mode, g, two_alpha, Z, p->tw);
         else
-            k_ray_fft<M, C::TPL, C::LPC1, MAXR, NC><<<dim3((V + C::LPC1 - 1) / C::LPC1, np), C::TPL * C::LPC1, C::S1, s>>>(
+            k_ray_fft<M, C::TPL, C::LPC1, MAXR, NC, C::ILV1><<<dim3((V + C::LPC1 - 1) / C::LPC1, np), C::TPL * C::LPC1, C::S1, s>>>(
                 sino, slices, p0, N, V, mode, g, two_alpha, Z, p->tw);
         bst_timing_mark(p, s, 0);
         if (kbg) {

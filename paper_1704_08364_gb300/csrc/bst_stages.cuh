@@ -384,22 +384,29 @@ __device__ __forceinline__ void ray_unit_prep(float2* smem, int j0, int V, int N
     fft_line<M, TPL, false, MAXR>(t, src, dst, sm, tw);
 }
 
+// Shared-memory stride between the lines of a ray unit: with the lines
+// interleaved over the lanes (ILV), the lines are skewed by 16 banks so that
+// lanes of two lines at the same offset do not share a bank.
+template <int M, bool ILV> __host__ __device__ constexpr int ray_line_stride() { return smem_line_len(M) + (ILV ? 8 : 0); }
+
 // P2 + P3 + P4 for lines j0 .. j0 + LPC - 1 of one slice pair (TPL * LPC
 // threads; tid the thread's index among them, -1: threadIdx.x; `sync` the
-// barrier that covers them)
-template <int M, int TPL, int LPC, int MAXR, int NC = 0, class SYNC = BlockSync>
+// barrier that covers them).  ILV: thread tid works on line tid % LPC, so a
+// warp holds the same bins of LPC consecutive angle rows, whose slots the
+// paired layout keeps in the same 128-byte lines.
+template <int M, int TPL, int LPC, int MAXR, int NC = 0, class SYNC = BlockSync, bool ILV = false>
 __device__ __forceinline__ void ray_unit(float2* smem, int j0, int V, int N, const float* __restrict__ ya,
                                          const float* __restrict__ yb, int mode, const float* __restrict__ g,
                                          float two_alpha, float2* __restrict__ Zp, const float2* __restrict__ tw,
                                          const SYNC& sync = SYNC(), int tid = -1) {
     if (tid < 0) tid = threadIdx.x;
-    const int line = tid / TPL, t = tid % TPL;
+    const int line = ILV ? tid % LPC : tid / TPL, t = ILV ? tid / LPC : tid % TPL;
     const int j = j0 + line;
     const bool live = j < V;
     const int jj = live ? j : 0;
     RaySrc<NC> src{ya + (size_t)jj * N, yb ? yb + (size_t)jj * N : nullptr, N, M, live};
     SpecDst dst{Zp, jj, V, g, M, mode, two_alpha, live};
-    SmemLine sm{smem + line * smem_line_len(M)};
+    SmemLine sm{smem + line * ray_line_stride<M, ILV>()};
     fft_line<M, TPL, false, MAXR>(t, src, dst, sm, tw, sync);
 }
 

@@ -4,8 +4,8 @@
 // can read their register and spill figures from ptxas.
 #include "bst_forward.cuh"
 
-template __global__ void bst::k_ray_fft<4096, 256, 1, 16, 2048>(const float*, int, int, int, int, int, const float*,
-                                                                 float, float2*, const float2*);
+template __global__ void bst::k_ray_fft<4096, 256, 2, 16, 2048, true>(const float*, int, int, int, int, int,
+                                                                       const float*, float, float2*, const float2*);
 template __global__ void bst::k_grid_col<4096, 256, 1, 16, 2048>(const float2*, int, int, const int*, const float2*,
                                                                   float2*, const float2*, int);
 template __global__ void bst::k_grid_col_paired<4096, 256, 1, 16, 2048>(const float2*, int, int, const int*,
