@@ -554,11 +554,28 @@ __device__ __forceinline__ void grid_unit_paired(float2* smem, int q0, int V, in
             selA[u] = up != sA;
             selB[u] = up != sB;
             const bool k1ok = ok && k0 + 1 < H;
-            const int k1 = k1ok ? k0 + 1 : k0;
-            z[u][0] = ok ? __ldg(Z2 + paired_slot(rowA, k0, H, V)) : zero4;
-            z[u][1] = k1ok ? __ldg(Z2 + paired_slot(rowA, k1, H, V)) : zero4;
-            z[u][2] = ok ? __ldg(Z2 + paired_slot(rowB, k0, H, V)) : zero4;
-            z[u][3] = k1ok ? __ldg(Z2 + paired_slot(rowB, k1, H, V)) : zero4;
+            // slots of the four taps: away from the seam both rows lie in the
+            // paired storage and the other three are fixed offsets from the
+            // first (next bin: +1, or +5 into the next group of four; next
+            // row: +4 within a line, 2H - 4 from an odd row to the next line)
+            int a0, a1, b0, b1;
+            if (!sA && !sB && rowA + 1 < (V & ~1)) {
+                a0 = paired_slot(rowA, k0, H, V);
+                a1 = a0 + ((k0 & 3) == 3 ? 5 : 1);
+                const int dr = (rowA & 1) ? 2 * H - 4 : 4;
+                b0 = a0 + dr;
+                b1 = a1 + dr;
+            } else {
+                const int k1 = k1ok ? k0 + 1 : k0;
+                a0 = paired_slot(rowA, k0, H, V);
+                a1 = paired_slot(rowA, k1, H, V);
+                b0 = paired_slot(rowB, k0, H, V);
+                b1 = paired_slot(rowB, k1, H, V);
+            }
+            z[u][0] = ok ? __ldg(Z2 + a0) : zero4;
+            z[u][1] = k1ok ? __ldg(Z2 + a1) : zero4;
+            z[u][2] = ok ? __ldg(Z2 + b0) : zero4;
+            z[u][3] = k1ok ? __ldg(Z2 + b1) : zero4;
         }
 #pragma unroll
         for (int u = 0; u < PS; ++u) {
