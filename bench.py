@@ -97,7 +97,7 @@ STAGE_NAMES = {0: "k_ray_fft", 1: "k_grid_col", 2: "k_row_ifft", 3: "k_ss_filter
 
 # DRAM bytes (read + write) per launch of each forward kernel from one ncu
 # capture of the dram__bytes_read.sum and dram__bytes_write.sum counters on
-# the volume-2048 geometry (8 slices, cold cache, one launch each), keyed by
+# the volume-2048 geometry (16 slices: one launch of 8 pairs each, cold cache), keyed by
 # a SHA-256 over the kernels' device-code headers (the host launcher lives in
 # another file, so host-only edits keep the record) and by the launch shape
 # that the capture ran.  A record applies only while the device code hashes
@@ -271,6 +271,38 @@ def workload_config(args, world: int) -> dict:
                    "inputs (%.3f GiB) fit in L2: no flush between steps") % (per_gpu * V * N * 4 / 2**30),
             "parallelism": (f"slices, {world} GPU(s), one volume split in whole-pair ranges" if strong else
                             f"slices, {world} GPU(s), one volume per GPU")}
+
+
+def link_probe(h_a, h_b, dev, nbytes: int = 1 << 30) -> dict:
+    """Host-link rates (GB/s) with pinned buffers: upload alone, download
+    alone, and both at once on two streams (per direction), best of three."""
+    import torch
+    n = min(nbytes // 4, h_a.numel(), h_b.numel())
+    ha, hb = h_a.view(-1)[:n], h_b.view(-1)[:n]
+    da = torch.empty(n, dtype=torch.float32, device=dev)
+    db = torch.empty(n, dtype=torch.float32, device=dev)
+    s1, s2 = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def best(fn):
+        ts = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t)
+        return 4 * n / min(ts) / 1e9
+
+    def both():
+        with torch.cuda.stream(s1):
+            da.copy_(ha, non_blocking=True)
+        with torch.cuda.stream(s2):
+            hb.copy_(db, non_blocking=True)
+
+    out = {"h2d_gbs": best(lambda: da.copy_(ha, non_blocking=True)),
+           "d2h_gbs": best(lambda: hb.copy_(db, non_blocking=True)), "both_gbs": best(both)}
+    del da, db
+    return out
 
 
 def _event_ms(fn, steps, warmup=2):
@@ -516,6 +548,11 @@ def run_ours(args, rank, world):
                "d2h_bytes_per_step": world * es * N * N * 4, "slices": world * es, "ms_per_step": dt * 1e3,
                "best_ms": 1e3 * min(per_step), "worst_ms": 1e3 * max(per_step),
                "api": "bst_fbp_host (pinned host buffers, chunked copy/compute overlap)"}
+        # the host link right after: its rates bound e2e from below (the
+        # link is shared with other jobs on the node, so it varies by run)
+        link = link_probe(h_in, h_out, dev)
+        link["floor_ms"] = 1e3 * max(es * V * N * 4, es * N * N * 4) / (link["both_gbs"] * 1e9)
+        e2e["link"] = link
         del h_in, h_out
     except Exception as ex:  # pragma: no cover - host memory limits
         e2e = {"value": None, "unit": UNIT, "error": str(ex)[:200]}
