@@ -581,20 +581,18 @@ __device__ __forceinline__ void grid_unit_paired(float2* smem, int q0, int V, in
         for (int u = 0; u < PS; ++u) {
             const int ridx = lt + (i + u) * NT;
             const float ft = fc[u].x, fk = fc[u].y;
-            // halves of each slot for the point (p) and its mirror (m)
+            // radial interpolation of whole slots (both halves: Z[.][+k] and
+            // Z[.][-k]), then the halves of each row for the point (p) and its
+            // mirror (m)
             const float4 a0 = z[u][0], a1 = z[u][1], b0 = z[u][2], b1 = z[u][3];
-            const float2 pa0 = selA[u] ? make_float2(a0.x, a0.y) : make_float2(a0.z, a0.w);
-            const float2 ma0 = selA[u] ? make_float2(a0.z, a0.w) : make_float2(a0.x, a0.y);
-            const float2 pa1 = selA[u] ? make_float2(a1.x, a1.y) : make_float2(a1.z, a1.w);
-            const float2 ma1 = selA[u] ? make_float2(a1.z, a1.w) : make_float2(a1.x, a1.y);
-            const float2 pb0 = selB[u] ? make_float2(b0.x, b0.y) : make_float2(b0.z, b0.w);
-            const float2 mb0 = selB[u] ? make_float2(b0.z, b0.w) : make_float2(b0.x, b0.y);
-            const float2 pb1 = selB[u] ? make_float2(b1.x, b1.y) : make_float2(b1.z, b1.w);
-            const float2 mb1 = selB[u] ? make_float2(b1.z, b1.w) : make_float2(b1.x, b1.y);
-            const float2 pA = make_float2(fmaf(fk, pa1.x - pa0.x, pa0.x), fmaf(fk, pa1.y - pa0.y, pa0.y));
-            const float2 pB = make_float2(fmaf(fk, pb1.x - pb0.x, pb0.x), fmaf(fk, pb1.y - pb0.y, pb0.y));
-            const float2 mA = make_float2(fmaf(fk, ma1.x - ma0.x, ma0.x), fmaf(fk, ma1.y - ma0.y, ma0.y));
-            const float2 mB = make_float2(fmaf(fk, mb1.x - mb0.x, mb0.x), fmaf(fk, mb1.y - mb0.y, mb0.y));
+            const float4 A = make_float4(fmaf(fk, a1.x - a0.x, a0.x), fmaf(fk, a1.y - a0.y, a0.y),
+                                         fmaf(fk, a1.z - a0.z, a0.z), fmaf(fk, a1.w - a0.w, a0.w));
+            const float4 B = make_float4(fmaf(fk, b1.x - b0.x, b0.x), fmaf(fk, b1.y - b0.y, b0.y),
+                                         fmaf(fk, b1.z - b0.z, b0.z), fmaf(fk, b1.w - b0.w, b0.w));
+            const float2 pA = selA[u] ? make_float2(A.x, A.y) : make_float2(A.z, A.w);
+            const float2 mA = selA[u] ? make_float2(A.z, A.w) : make_float2(A.x, A.y);
+            const float2 pB = selB[u] ? make_float2(B.x, B.y) : make_float2(B.z, B.w);
+            const float2 mB = selB[u] ? make_float2(B.z, B.w) : make_float2(B.x, B.y);
             l0.store(ridx, make_float2(fmaf(ft, pB.x - pA.x, pA.x), fmaf(ft, pB.y - pA.y, pA.y)));
             l1.store(ridx, q == 0 ? make_float2(0.f, 0.f)
                                   : make_float2(fmaf(ft, mB.x - mA.x, mA.x), fmaf(ft, mB.y - mA.y, mA.y)));
