@@ -502,6 +502,7 @@ __device__ __forceinline__ void grid_unit_paired(float2* smem, int q0, int V, in
     constexpr int NT = 2 * TPL;
     constexpr int PPT = M / NT;   // point pairs per thread
     static_assert(PPT % PS == 0, "point pairs per step");
+    static_assert(PPT % 2 == 0 && (PPT / 2) * NT == (M >> 1), "half the rows of a column per half of the steps");
     static_assert(NT < 32 || NT % 32 == 0, "groups of 32 or more threads are whole warps");
     if (tid < 0) tid = threadIdx.x;
     const int g = tid / NT;
@@ -540,12 +541,14 @@ __device__ __forceinline__ void grid_unit_paired(float2* smem, int q0, int V, in
         bool selA[PS], selB[PS];
 #pragma unroll
         for (int u = 0; u < PS; ++u) {
-            const int ridx = lt + (i + u) * NT;
             const int Jt = jc[u] >> 16;
             const int k0 = jc[u] & 0xffff;
             // a table bracket >= -1 means the point is inside the band and not the origin
             const bool ok = live && Jt >= -1;
-            const bool up = signed_freq(ridx, M) >= 0;   // kappa = +rho for the point (q, r'), q >= 0
+            // kappa = +rho for the point (q, r'), q >= 0, iff r' >= 0, i.e. its row
+            // index lt + (i + u) NT < M/2: with 0 <= lt < NT that is exactly
+            // (i + u) NT < M/2, fixed per unrolled step
+            const bool up = (i + u) < PPT / 2;
             const int J = ok ? Jt : 0;
             const bool sA = J < 0, sB = J + 1 >= V;
             const int rowA = sA ? V - 1 : J;
