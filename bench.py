@@ -106,11 +106,11 @@ STAGE_NAMES = {0: "k_ray_fft", 1: "k_grid_col", 2: "k_row_ifft", 3: "k_ss_filter
 KERNEL_SOURCES = ["paper_1704_08364_gb300/csrc/bst_forward.cuh", "paper_1704_08364_gb300/csrc/bst_stages.cuh",
                   "paper_1704_08364_gb300/csrc/bst_fft.cuh", "paper_1704_08364_gb300/csrc/bst_geo.cuh"]
 CAPTURED_TRAFFIC = [
-    {"sha": "a440d8c8a9af9c00b45e6311661baf0de31bb575d681428e46bd85fb02ae482c",
+    {"sha": "ca3ac93b5731d2203ceee25ca2bb8a8dc9e788382746fa9d6e2fbcbd64c9a013",
      "rays": 2048, "pad": 2,
      "shape": {"layout": "paired", "chunk_pairs": 8, "pair_fast": 1, "max_radix": 16},
-     "bytes": {"k_ray_fft": 283127040 + 485289728, "k_grid_col": 629517312 + 487033856,
-               "k_row_ifft": 536956672 + 237107968}},
+     "bytes": {"k_ray_fft": 280852480 + 484005376, "k_grid_col": 629304064 + 487205632,
+               "k_row_ifft": 536913408 + 237415168}},
 ]
 
 
