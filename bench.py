@@ -108,7 +108,7 @@ KERNEL_SOURCES = ["paper_1704_08364_gb300/csrc/bst_forward.cuh", "paper_1704_083
 CAPTURED_TRAFFIC = [
     {"sha": "ca3ac93b5731d2203ceee25ca2bb8a8dc9e788382746fa9d6e2fbcbd64c9a013",
      "rays": 2048, "pad": 2,
-     "shape": {"layout": "paired", "chunk_pairs": 8, "pair_fast": 1, "max_radix": 16},
+     "shape": {"layout": "paired", "chunk_pairs": 8, "pair_fast": 1, "max_radix": 16, "grid_xchg": 0},
      "bytes": {"k_ray_fft": 280852480 + 484005376, "k_grid_col": 629304064 + 487205632,
                "k_row_ifft": 536913408 + 237415168}},
 ]
@@ -127,7 +127,7 @@ def captured_traffic(kernel: str, rays: int, pad: int, shape: dict):
     """Stored DRAM bytes per launch of `kernel` for this geometry and launch
     shape, or None when no capture of the current device code matches."""
     sha = device_code_sha()
-    keys = ("layout", "chunk_pairs", "pair_fast", "max_radix")
+    keys = ("layout", "chunk_pairs", "pair_fast", "max_radix", "grid_xchg")
     for c in CAPTURED_TRAFFIC:
         if (c["sha"] == sha and c["rays"] == rays and c["pad"] == pad
                 and all(c["shape"][k] == shape[k] for k in keys)):

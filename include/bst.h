@@ -83,6 +83,9 @@ typedef struct {
     int chunk_pairs;  /* slice pairs per launch of each stage, 1..256 */
     int pair_fast;    /* 1: gridding blocks ordered pair-fastest within a chunk */
     int max_lanes;    /* streams alternating chunks, 1 or 2 */
+    int grid_xchg;    /* paired layout only: 1 feeds the first column-FFT pass of both
+                         columns of a pair from registers (partner lanes swap the halves
+                         of their gathered point pairs), 0 goes through shared memory */
 } bst_fwd_config_t;
 
 typedef struct bst_plan_s* bst_plan_t;

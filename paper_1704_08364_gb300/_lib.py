@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "libbst.so")
 class FwdConfig(ctypes.Structure):
     """bst_fwd_config_t: the launch shape of the forward path."""
     _fields_ = [("max_radix", ctypes.c_int), ("layout", ctypes.c_int), ("chunk_pairs", ctypes.c_int),
-                ("pair_fast", ctypes.c_int), ("max_lanes", ctypes.c_int)]
+                ("pair_fast", ctypes.c_int), ("max_lanes", ctypes.c_int), ("grid_xchg", ctypes.c_int)]
 
 
 c_plan = ctypes.c_void_p

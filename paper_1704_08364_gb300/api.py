@@ -112,11 +112,13 @@ class Plan:
     @property
     def forward_config(self) -> dict:
         """Launch shape of the forward path (bst_plan_get_forward_config):
-        max_radix, layout ("packed" or "paired"), chunk_pairs, pair_fast, max_lanes."""
+        max_radix, layout ("packed" or "paired"), chunk_pairs, pair_fast, max_lanes,
+        grid_xchg (1: register-fed paired gridding, 0: through shared memory)."""
         c = _lib.FwdConfig()
         _check(self._lib.bst_plan_get_forward_config(self._h, ctypes.byref(c)), "bst_plan_get_forward_config")
         return {"max_radix": c.max_radix, "layout": "paired" if c.layout == 1 else "packed",
-                "chunk_pairs": c.chunk_pairs, "pair_fast": c.pair_fast, "max_lanes": c.max_lanes}
+                "chunk_pairs": c.chunk_pairs, "pair_fast": c.pair_fast, "max_lanes": c.max_lanes,
+                "grid_xchg": c.grid_xchg}
 
     def set_forward_config(self, **kw):
         """Change fields of the launch shape (bst_plan_set_forward_config);
@@ -125,7 +127,8 @@ class Plan:
         cur.update(kw)
         layout = {"packed": 0, "paired": 1}.get(cur["layout"], cur["layout"])
         c = _lib.FwdConfig(int(cur["max_radix"]), int(layout),
-                           int(cur["chunk_pairs"]), int(cur["pair_fast"]), int(cur["max_lanes"]))
+                           int(cur["chunk_pairs"]), int(cur["pair_fast"]), int(cur["max_lanes"]),
+                           int(cur["grid_xchg"]))
         _check(self._lib.bst_plan_set_forward_config(self._h, ctypes.byref(c)), "bst_plan_set_forward_config")
         return self
 

@@ -20,6 +20,9 @@
 //   k_grid_col_paired  the same from the paired layout of Z (one 16-byte
 //               slot (Z[k], Z[-k]) per bin serves a point and its mirror),
 //               which the ray kernel writes when the plan asks for it.
+//   k_grid_col_xchg  the same for one column pair per block with the first
+//               FFT pass of both columns fed from registers (partner lanes
+//               swap the halves of their gathered point pairs).
 //   k_row_ifft  the row half of P6 + P7 + P8: inverse FFT along c' for four
 //               rows at a time, keep the N central columns, scale by
 //               dt dw^2 = N / (2 M^2), write Re to slice a and Im to slice b.
@@ -95,6 +98,20 @@ __global__ void __launch_bounds__(2 * TPL * CPC, (2 * TPL * CPC <= 1024) ? 1024 
     grid_unit_paired<M, TPL, CPC, MAXR, NC>(smem, cg * CPC, V, N,
                                             reinterpret_cast<const float4*>(Z + (size_t)pl * V * M), gJ, gF,
                                             T + (size_t)pl * ((N + 3) / 4) * 4 * M, tw);
+}
+
+// the same for one column pair per block, the first FFT pass of both columns
+// fed from registers (grid_unit_xchg)
+template <int M, int TPL, int MAXR, int NC = 0, int PS = 2>
+__global__ void __launch_bounds__(2 * TPL, (2 * TPL <= 1024) ? 1024 / (2 * TPL) : 1)
+    k_grid_col_xchg(const float2* __restrict__ Z, int V, int N, const int* __restrict__ gJ,
+                    const float2* __restrict__ gF, float2* __restrict__ T, const float2* __restrict__ tw,
+                    int pair_fast) {
+    extern __shared__ float2 smem[];
+    const int pl = pair_fast ? blockIdx.x : blockIdx.y;
+    const int cq = pair_fast ? blockIdx.y : blockIdx.x;
+    grid_unit_xchg<M, TPL, MAXR, NC, PS>(smem, cq, V, N, reinterpret_cast<const float4*>(Z + (size_t)pl * V * M), gJ,
+                                         gF, T + (size_t)pl * ((N + 3) / 4) * 4 * M, tw);
 }
 
 template <int M, int TPL, int TPC, int MAXR, int NC = 0>

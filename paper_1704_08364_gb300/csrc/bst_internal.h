@@ -50,6 +50,7 @@ struct bst_plan_s {
     int fwd_layout = 0;             // BST_LAYOUT_PACKED or BST_LAYOUT_PAIRED (autotuned)
     int pair_fast = 0;              // gridding blocks ordered pair-fastest (autotuned)
     int max_lanes = 2;              // streams alternating chunks (1 or 2)
+    int grid_xchg = 0;              // register-fed paired gridding (0 or 1; autotuned)
     // two plan-owned streams that alternate chunks of the forward path (fork
     // from and join back to the caller's stream with events), created on first use
     cudaStream_t lane[3] = {nullptr, nullptr, nullptr};

@@ -34,8 +34,19 @@ template <int M> struct FwdCfg {
     static constexpr size_t S2 = (size_t)CPC * smem_line_len(M) * sizeof(float2);
     static constexpr int CPCP = paired_cpc<M>();
     static constexpr size_t S2P = (size_t)2 * CPCP * smem_line_len(M) * sizeof(float2);
+    // the register-fed gridding kernel: half-warps of 16 consecutive threads of a column
+    static constexpr bool XCHG_OK = TPL % 16 == 0;
+    static constexpr size_t S2X = (size_t)2 * smem_line_len(M) * sizeof(float2);
     static constexpr size_t S3 = (size_t)4 * TPC * row_line_stride<M>() * sizeof(float2);
 };
+
+// the shared-memory opt-in of the register-fed gridding kernel, where it exists
+template <int M, int MAXR, int NC>
+static bool set_smem_xchg() {
+    using C = FwdCfg<M>;
+    if constexpr (C::XCHG_OK) return set_smem(k_grid_col_xchg<M, C::TPL, MAXR, NC>, C::S2X);
+    return true;
+}
 
 template <int M, int MAXR, int NC>
 bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int mode, const float* g, float* vol,
@@ -47,6 +58,7 @@ bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int 
                    set_smem(k_ray_fft_prep<M, C::TPL, C::LPC1, MAXR, NC>, C::S1) &&
                    set_smem(k_grid_col<M, C::TPL, C::CPC, MAXR, NC>, C::S2) &&
                    set_smem(k_grid_col_paired<M, C::TPL, C::CPCP, MAXR, NC>, C::S2P) &&
+                   set_smem_xchg<M, MAXR, NC>() &&
                    set_smem(k_row_ifft<M, C::TPL, C::TPC, MAXR, NC>, C::S3);
         }))
         return BST_ERR_CUDA;
@@ -94,6 +106,11 @@ bst_status_t launch_forward_M(bst_plan_s* p, const float* sino, int slices, int 
         if (kbg) {
             const bst_status_t ks = bst_launch_kb_col(p, Z, T, np, s);
             if (ks != BST_OK) return ks;
+        } else if (paired && C::XCHG_OK && p->grid_xchg) {
+            if constexpr (C::XCHG_OK) {
+                k_grid_col_xchg<M, C::TPL, MAXR, NC><<<pf ? dim3(np, M / 2) : dim3(M / 2, np), 2 * C::TPL, C::S2X, s>>>(
+                    Z, V, N, p->geo_J, p->geo_f, T, p->tw, pf);
+            }
         } else if (paired) {
             const int ncg = (M / 2 + C::CPCP - 1) / C::CPCP;
             k_grid_col_paired<M, C::TPL, C::CPCP, MAXR, NC>

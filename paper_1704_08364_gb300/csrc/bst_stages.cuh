@@ -639,6 +639,148 @@ __device__ __forceinline__ void grid_unit_paired(float2* smem, int q0, int V, in
     fft_line<M, TPL, true, MAXR>(t, line, dst, line, tw, sync);
 }
 
+// P0 + P5 + column P6 for one column pair (q, -q) from the paired spectrum
+// layout (2 TPL threads), with the first FFT pass of both columns fed from
+// registers instead of through shared memory.  Thread (warp w, lane l) is
+// thread t = 16 w + l % 16 of column q (l < 16) or of column -q (l >= 16,
+// stored index-reversed), so a warp holds the same 16 consecutive t of both
+// columns.  The first pass of thread t needs rows t + i TPL, i < M / TPL, of
+// its column (fft_line_regs); the lane of column q gathers the point pairs of
+// the even i, its partner lane l ^ 16 those of the odd i.  Each point pair
+// gives the value of column q (the point) and of column -q (its mirror): a
+// lane keeps its own column's value and swaps the other with its partner
+// (shfl.xor 16), so that each lane then holds all its first-pass inputs.
+// The taps of a quarter-warp (the unit in which 16-byte loads are served)
+// are those of 8 consecutive rows of one column, as in grid_unit_paired.
+// PS point pairs per gather step.
+template <int M, int TPL, int MAXR, int NC = 0, int PS = 2>
+__device__ __forceinline__ void grid_unit_xchg(float2* smem, int q, int V, int N, const float4* __restrict__ Z2,
+                                               const int* __restrict__ gJ, const float2* __restrict__ gF,
+                                               float2* __restrict__ Tp, const float2* __restrict__ tw) {
+    constexpr int H = M >> 1;
+    constexpr int PPL = M / TPL;   // first-pass inputs per thread (16, or 12 for lengths 3 * 2^a)
+    constexpr int PPT = PPL / 2;   // point pairs gathered per thread
+    static_assert(TPL % 16 == 0, "half-warps of 16 consecutive threads of a column");
+    static_assert(PPL % 4 == 0 && PPT % PS == 0, "steps of the upper and lower half rows");
+    const int lane = threadIdx.x & 31;
+    const int h = lane >> 4;                                   // 0: column q, 1: column -q
+    const int t = ((threadIdx.x >> 5) << 4) + (lane & 15);     // thread index within the column
+    const bool live = q < H;
+    const int* gJq = gJ + (size_t)(live ? q : 0) * M;
+    const float2* gFq = gF + (size_t)(live ? q : 0) * M;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    // xe[i] = input 2 i, xo[i] = input 2 i + 1 of the thread's first pass
+    float2 xe[PPT], xo[PPT];
+    int jn[PS];
+    float2 fn[PS];
+#pragma unroll
+    for (int u = 0; u < PS; ++u) {
+        jn[u] = __ldg(gJq + t + (2 * u + h) * TPL);
+        fn[u] = __ldg(gFq + t + (2 * u + h) * TPL);
+    }
+#pragma unroll
+    for (int i = 0; i < PPT; i += PS) {
+        int jc[PS];
+        float2 fc[PS];
+#pragma unroll
+        for (int u = 0; u < PS; ++u) {
+            jc[u] = jn[u];
+            fc[u] = fn[u];
+        }
+        if (i + PS < PPT) {
+#pragma unroll
+            for (int u = 0; u < PS; ++u) {
+                jn[u] = __ldg(gJq + t + (2 * (i + PS + u) + h) * TPL);
+                fn[u] = __ldg(gFq + t + (2 * (i + PS + u) + h) * TPL);
+            }
+        }
+        float4 z[PS][4];
+        bool selA[PS], selB[PS];
+#pragma unroll
+        for (int u = 0; u < PS; ++u) {
+            const int Jt = jc[u] >> 16;
+            const int k0 = jc[u] & 0xffff;
+            const bool ok = live && Jt >= -1;
+            // the row t + (2 (i + u) + h) TPL is below M/2 (kappa = +rho for
+            // the point) iff 2 (i + u) + h < PPL / 2, i.e. i + u < PPL / 4 for
+            // both h: fixed per unrolled step
+            const bool up = (i + u) < PPL / 4;
+            const int J = ok ? Jt : 0;
+            const bool sA = J < 0, sB = J + 1 >= V;
+            const int rowA = sA ? V - 1 : J;
+            const int rowB = sB ? 0 : J + 1;
+            selA[u] = up != sA;
+            selB[u] = up != sB;
+            const bool k1ok = ok && k0 + 1 < H;
+            int a0, a1, b0, b1;
+            if (!sA && !sB && rowA + 1 < (V & ~1)) {
+                a0 = paired_slot(rowA, k0, H, V);
+                a1 = a0 + ((k0 & 3) == 3 ? 5 : 1);
+                const int dr = (rowA & 1) ? 2 * H - 4 : 4;
+                b0 = a0 + dr;
+                b1 = a1 + dr;
+            } else {
+                const int k1 = k1ok ? k0 + 1 : k0;
+                a0 = paired_slot(rowA, k0, H, V);
+                a1 = paired_slot(rowA, k1, H, V);
+                b0 = paired_slot(rowB, k0, H, V);
+                b1 = paired_slot(rowB, k1, H, V);
+            }
+            z[u][0] = ok ? __ldg(Z2 + a0) : zero4;
+            z[u][1] = k1ok ? __ldg(Z2 + a1) : zero4;
+            z[u][2] = ok ? __ldg(Z2 + b0) : zero4;
+            z[u][3] = k1ok ? __ldg(Z2 + b1) : zero4;
+        }
+#pragma unroll
+        for (int u = 0; u < PS; ++u) {
+            const float ft = fc[u].x, fk = fc[u].y;
+            const float4 a0 = z[u][0], a1 = z[u][1], b0 = z[u][2], b1 = z[u][3];
+            const float4 A = make_float4(fmaf(fk, a1.x - a0.x, a0.x), fmaf(fk, a1.y - a0.y, a0.y),
+                                         fmaf(fk, a1.z - a0.z, a0.z), fmaf(fk, a1.w - a0.w, a0.w));
+            const float4 B = make_float4(fmaf(fk, b1.x - b0.x, b0.x), fmaf(fk, b1.y - b0.y, b0.y),
+                                         fmaf(fk, b1.z - b0.z, b0.z), fmaf(fk, b1.w - b0.w, b0.w));
+            const float2 pA = selA[u] ? make_float2(A.x, A.y) : make_float2(A.z, A.w);
+            const float2 mA = selA[u] ? make_float2(A.z, A.w) : make_float2(A.x, A.y);
+            const float2 pB = selB[u] ? make_float2(B.x, B.y) : make_float2(B.z, B.w);
+            const float2 mB = selB[u] ? make_float2(B.z, B.w) : make_float2(B.x, B.y);
+            const float2 P = make_float2(fmaf(ft, pB.x - pA.x, pA.x), fmaf(ft, pB.y - pA.y, pA.y));
+            const float2 Q = q == 0 ? make_float2(0.f, 0.f)
+                                    : make_float2(fmaf(ft, mB.x - mA.x, mA.x), fmaf(ft, mB.y - mA.y, mA.y));
+            // keep the own column's value, swap the other with the partner lane
+            const float2 own = h ? Q : P, oth = h ? P : Q;
+            const float2 rcv = make_float2(__shfl_xor_sync(0xffffffffu, oth.x, 16),
+                                           __shfl_xor_sync(0xffffffffu, oth.y, 16));
+            xe[i + u] = h ? rcv : own;
+            xo[i + u] = h ? own : rcv;
+        }
+    }
+    float2 x[PPL];
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) {
+        x[2 * i] = xe[i];
+        x[2 * i + 1] = xo[i];
+    }
+    // the origin (row 0 of column q = 0, input 0 of thread 0, the gather gave 0
+    // there) is single-valued: mean over angles of the DC bin, by warp 0
+    if (live && q == 0 && threadIdx.x < 32) {
+        float sx = 0.f, sy = 0.f;
+        for (int j = lane; j < V; j += 32) {
+            const float4 zz = __ldg(Z2 + paired_slot(j, 0, H, V));
+            sx += zz.x;
+            sy += zz.y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        }
+        if (lane == 0) x[0] = make_float2(sx / (float)V, sy / (float)V);
+    }
+    const SmemLine sm{smem + h * smem_line_len(M)};
+    const ColDst<NC> dst{Tp, N, M, h == 0 ? q : (q == 0 ? H : M - q), h == 1 && q != 0, live};
+    fft_line_regs<M, TPL, true, MAXR>(t, x, dst, sm, tw);
+}
+
 // row P6 + P7 + P8 for row tiles rb0 .. rb0 + TPC - 1 of RPT rows each (RPT TPL
 // TPC threads; tid and sync as for ray_unit): tile b holds rows RPT b ..
 // RPT b + RPT - 1.  RPT = 4 reads T in whole 32-byte groups of four rows; a

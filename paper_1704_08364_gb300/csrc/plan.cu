@@ -344,13 +344,14 @@ bst_status_t bst_plan_set_forward_config(bst_plan_t p, const bst_fwd_config_t* c
     if ((c->max_radix != 8 && c->max_radix != 16) ||
         (c->layout != BST_LAYOUT_PACKED && c->layout != BST_LAYOUT_PAIRED) || c->chunk_pairs < 1 ||
         c->chunk_pairs > 256 || (c->pair_fast != 0 && c->pair_fast != 1) || c->max_lanes < 1 ||
-        c->max_lanes > bsth::kMaxLanes)
+        c->max_lanes > bsth::kMaxLanes || (c->grid_xchg != 0 && c->grid_xchg != 1))
         return BST_ERR_INVALID_ARGUMENT;
     p->maxr = c->max_radix;
     p->fwd_layout = c->layout;
     p->chunk_pairs = c->chunk_pairs;
     p->pair_fast = c->pair_fast;
     p->max_lanes = c->max_lanes;
+    p->grid_xchg = c->grid_xchg;
     return BST_OK;
 }
 
@@ -361,22 +362,25 @@ bst_status_t bst_plan_get_forward_config(bst_plan_t p, bst_fwd_config_t* c) {
     c->chunk_pairs = p->chunk_pairs;
     c->pair_fast = p->pair_fast;
     c->max_lanes = p->max_lanes;
+    c->grid_xchg = p->grid_xchg;
     return BST_OK;
 }
 
 // The candidate launch shapes of the autotuner: radix 16 or 8, the packed or
-// (bilinear plans) paired spectrum layout, and the default chunk in
-// column-fastest order or pair-fastest order; where the default chunk is a
-// single pair (the workspace of one pair exceeds L2), also chunks of 2, 4
-// and 8 pairs: the launches then fill more waves of blocks, at the price of a
-// workspace (and intermediates in HBM) that grows with the chunk.  The lane
-// count stays the plan's.
+// (bilinear plans) paired spectrum layout, for the paired layout the gather
+// through shared memory or into registers, and the default chunk in column-fastest
+// order or pair-fastest order; where the default chunk is a single pair (the
+// workspace of one pair exceeds L2), also chunks of 2, 4 and 8 pairs: the
+// launches then fill more waves of blocks, at the price of a workspace (and
+// intermediates in HBM) that grows with the chunk.  The lane count stays the
+// plan's.
 static std::vector<bst_fwd_config_t> tune_candidates(const bst_plan_s* p) {
     std::vector<bst_fwd_config_t> out;
-    const int layouts = p->grid_kind == BST_GRID_BILINEAR ? 2 : 1;
+    const int layouts = p->grid_kind == BST_GRID_BILINEAR ? 3 : 1;   // packed, paired, paired + exchange
     for (int r : {16, 8})
-        for (int l = 0; l < layouts; ++l) {
-            bst_fwd_config_t c{r, l, p->chunk_default, 0, p->max_lanes};
+        for (int lg = 0; lg < layouts; ++lg) {
+            const int l = lg == 0 ? BST_LAYOUT_PACKED : BST_LAYOUT_PAIRED;
+            bst_fwd_config_t c{r, l, p->chunk_default, 0, p->max_lanes, lg == 2 ? 1 : 0};
             out.push_back(c);
             if (p->chunk_default == 1) {
                 for (int ch : {2, 4, 8}) {

@@ -12,3 +12,5 @@ template __global__ void bst::k_grid_col_paired<4096, 256, 1, 16, 2048>(const fl
                                                                          const float2*, float2*, const float2*, int);
 template __global__ void bst::k_row_ifft<4096, 256, 1, 16, 2048>(const float2*, int, int, int, float, float*,
                                                                   const float2*, const float*);
+template __global__ void bst::k_grid_col_xchg<4096, 256, 16, 2048, 2>(const float2*, int, int, const int*,
+                                                                       const float2*, float2*, const float2*, int);

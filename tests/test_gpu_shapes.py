@@ -1,5 +1,6 @@
 """Every launch shape of the forward path gives the oracle's result: radix
-schedule 16 or 8, packed or paired spectrum layout, chunks of one to three
+schedule 16 or 8, packed or paired spectrum layout (the paired gather through
+shared memory or into registers), chunks of one to three
 slice pairs in column- or pair-fastest block order, one or two lanes
 (bst_plan_set_forward_config), and the shape the autotuner picks.  The
 shapes change how the stages of Sec. 2 are tiled, never what they compute."""
@@ -22,9 +23,9 @@ def bst():
     return m
 
 
-SHAPES = [dict(max_radix=r, layout=l, chunk_pairs=c, pair_fast=f, max_lanes=n)
-          for r, l, (c, f), n in itertools.product((16, 8), ("packed", "paired"),
-                                                   ((1, 0), (2, 0), (2, 1), (3, 1)), (2, 1))]
+SHAPES = [dict(max_radix=r, layout=l, chunk_pairs=c, pair_fast=f, max_lanes=n, grid_xchg=x)
+          for r, (l, x), (c, f), n in itertools.product((16, 8), (("packed", 0), ("paired", 0), ("paired", 1)),
+                                                         ((1, 0), (2, 0), (2, 1), (3, 1)), (2, 1))]
 
 
 def _oracle(sino, theta, alpha, mode):
@@ -57,26 +58,29 @@ def test_every_launch_shape_matches_the_oracle(bst, N, V, alpha):
             assert_parity(got, refs[mode], what=f"N={N} V={V} a={alpha} {mode} {shape}")
 
 
-def test_paired_layout_at_2048_with_nonuniform_angles(bst):
+@pytest.mark.parametrize("grid_xchg", [0, 1])
+def test_paired_layout_at_2048_with_nonuniform_angles(bst, grid_xchg):
     """The paired layout's seam rows and radial taps at M = 4096: sorted random
     angles (first angle above 0, so the bracket below theta_0 is used), one
-    slice pair, both modes."""
+    slice pair, the gather through shared memory or into registers."""
     rng = np.random.default_rng(4096)
     N = V = 2048
     theta = np.sort(np.unique(rng.uniform(0.01, np.pi - 0.003, V + 16).astype(np.float32))[:V])
     sino = np.stack([synth.gaussian_noise(synth.ellipse_sinogram(synth.random_ellipses(rng), theta, N), rng)
                      for _ in range(2)]).astype(np.float32)
     plan = bst.Plan(N, theta, 2)
-    plan.set_forward_config(layout="paired", chunk_pairs=2, pair_fast=1)
+    plan.set_forward_config(layout="paired", chunk_pairs=2, pair_fast=1, grid_xchg=grid_xchg)
     d = torch.from_numpy(sino).cuda()
     got = plan.fbp(d).cpu().numpy()
     for s in range(2):
-        assert_parity(got[s], ob.fbp(sino[s].astype(np.float64), theta), what=f"paired 2048 slice {s}")
+        assert_parity(got[s], ob.fbp(sino[s].astype(np.float64), theta),
+                      what=f"paired 2048 slice {s} grid_xchg {grid_xchg}")
 
 
-def test_paired_layout_with_prep_stages_and_filter_taps(bst):
+@pytest.mark.parametrize("grid_xchg", [0, 1])
+def test_paired_layout_with_prep_stages_and_filter_taps(bst, grid_xchg):
     """bst_fbp_prep (normalization, centering, window) and learnable taps on
-    the paired layout."""
+    the paired layout, the gather through shared memory or into registers."""
     from oracle import prep
     N, V, S = 128, 96, 3
     rng = np.random.default_rng(19)
@@ -86,7 +90,7 @@ def test_paired_layout_with_prep_stages_and_filter_taps(bst):
     counts = flat[:, None, :] * np.exp(-y)
     g = rng.uniform(0.3, 1.4, 2 * N // 2).astype(np.float32)
     plan = bst.Plan(N, theta, 2)
-    plan.set_forward_config(layout="paired", chunk_pairs=2, pair_fast=1)
+    plan.set_forward_config(layout="paired", chunk_pairs=2, pair_fast=1, grid_xchg=grid_xchg)
     f = lambda a: torch.from_numpy(np.asarray(a, dtype=np.float32)).cuda()
     got = plan.fbp_prep(f(counts), flat=f(flat), shift=-2.3, kb_beta=3.0, kb_halfwidth=0.95, g=f(g)).cpu().numpy()
     for s in range(S):
@@ -115,7 +119,7 @@ def test_invalid_shapes_are_rejected_and_change_nothing(bst):
     plan = bst.Plan(64, synth.uniform_angles(64), 2)
     before = plan.forward_config
     for bad in (dict(max_radix=4), dict(layout=7), dict(chunk_pairs=0), dict(chunk_pairs=257),
-                dict(pair_fast=2), dict(max_lanes=0), dict(max_lanes=3)):
+                dict(pair_fast=2), dict(max_lanes=0), dict(max_lanes=3), dict(grid_xchg=2)):
         with pytest.raises(bst.BstError):
             plan.set_forward_config(**bad)
         assert plan.forward_config == before

@@ -1,7 +1,8 @@
 """Register and spill budget of the 2048^3 forward kernels, read from ptxas
 (-Xptxas -v) at compile time; no GPU needed.  A regression guard: the packed
-gridding kernel runs four 256-thread blocks per SM and the paired one two
-512-thread blocks (64 registers a thread either way), spilling at most a few
+gridding kernel runs four 256-thread blocks per SM and the paired and
+register-fed paired ones two 512-thread blocks (64 registers a thread in each
+case), spilling at most a few
 bytes; the FFT kernels spill nothing."""
 import os
 import re
@@ -30,13 +31,13 @@ def report(tmp_path_factory):
     res = {}
     # one block per kernel, from its "Compiling entry function" line to the next
     for block in txt.split("Compiling entry function")[1:]:
-        for name in ("k_ray_fft", "k_grid_col", "k_grid_col_paired", "k_row_ifft"):
+        for name in ("k_ray_fft", "k_grid_col", "k_grid_col_paired", "k_grid_col_xchg", "k_row_ifft"):
             if re.match(r"\s*'[^']*\d" + name + r"ILi4096", block):
                 regs = re.search(r"Used (\d+) registers", block)
                 spill = re.search(r"(\d+) bytes spill stores", block)
                 assert regs and spill, block
                 res[name] = (int(regs.group(1)), int(spill.group(1)))
-    assert sorted(res) == ["k_grid_col", "k_grid_col_paired", "k_ray_fft", "k_row_ifft"], txt
+    assert sorted(res) == ["k_grid_col", "k_grid_col_paired", "k_grid_col_xchg", "k_ray_fft", "k_row_ifft"], txt
     return res
 
 
@@ -47,7 +48,7 @@ def test_fft_kernels_do_not_spill(report):
 
 
 def test_gridding_kernels_keep_their_blocks_per_sm(report):
-    for name in ("k_grid_col", "k_grid_col_paired"):
+    for name in ("k_grid_col", "k_grid_col_paired", "k_grid_col_xchg"):
         regs, spill = report[name]
         assert regs <= 64, f"{name} uses {regs} registers"
         assert spill <= 32, f"{name} spills {spill} bytes"
