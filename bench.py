@@ -106,11 +106,11 @@ STAGE_NAMES = {0: "k_ray_fft", 1: "k_grid_col", 2: "k_row_ifft", 3: "k_ss_filter
 KERNEL_SOURCES = ["paper_1704_08364_gb300/csrc/bst_forward.cuh", "paper_1704_08364_gb300/csrc/bst_stages.cuh",
                   "paper_1704_08364_gb300/csrc/bst_fft.cuh", "paper_1704_08364_gb300/csrc/bst_geo.cuh"]
 CAPTURED_TRAFFIC = [
-    {"sha": "ca3ac93b5731d2203ceee25ca2bb8a8dc9e788382746fa9d6e2fbcbd64c9a013",
+    {"sha": "5182a6ef3146a9c4f464342e17da68624378eacd4d1d37d661da52193c60e7df",
      "rays": 2048, "pad": 2,
-     "shape": {"layout": "paired", "chunk_pairs": 8, "pair_fast": 1, "max_radix": 16, "grid_xchg": 0},
-     "bytes": {"k_ray_fft": 280852480 + 484005376, "k_grid_col": 629304064 + 487205632,
-               "k_row_ifft": 536913408 + 237415168}},
+     "shape": {"layout": "paired", "chunk_pairs": 8, "pair_fast": 1, "max_radix": 16, "grid_xchg": 1},
+     "bytes": {"k_ray_fft": 271184896 + 476406272, "k_grid_col": 629041664 + 486836480,
+               "k_row_ifft": 536912640 + 237447424}},
 ]
 
 

@@ -148,6 +148,36 @@ __host__ __device__ constexpr int radix_of(int M, int p, int MAXR = 16) {
     return 1 << bits;
 }
 
+// ---- per-pass twiddle tables ---------------------------------------------------
+//
+// Beside the base table tw[m] = exp(-2 pi i m / M), m < M, the plan stores for
+// each radix schedule (largest radix 16, then 8) and each pass p >= 1 (radix
+// R, sub-transform length NS) the pass's twiddles w^(k s), w = exp(-2 pi i /
+// (NS R)), at entry (s - 1) NS + k (s = 1..R-1, k < NS): the R - 1 twiddles of
+// butterfly k are NS apart, so the lanes of a warp (consecutive k) read them
+// coalesced.  Each entry equals tw[k s M / (NS R)].
+
+// sub-transform length before pass p of the schedule
+__host__ __device__ constexpr int pass_ns(int M, int p, int MAXR) {
+    return p == 0 ? 1 : pass_ns(M, p - 1, MAXR) * radix_of(M, p - 1, MAXR);
+}
+// entries of the tables of passes 1 .. p - 1 of the schedule
+__host__ __device__ constexpr int pass_tab_prefix(int M, int p, int MAXR) {
+    return p <= 1 ? 0 : pass_tab_prefix(M, p - 1, MAXR) + (radix_of(M, p - 1, MAXR) - 1) * pass_ns(M, p - 1, MAXR);
+}
+// passes of the schedule
+__host__ __device__ constexpr int pass_count(int M, int MAXR, int p = 0) {
+    return pass_ns(M, p, MAXR) >= M ? p : pass_count(M, MAXR, p + 1);
+}
+// offset in tw of the table of pass p of the schedule (16 first, then 8)
+__host__ __device__ constexpr int pass_tab_base(int M, int MAXR, int p) {
+    return M + (MAXR == 8 ? pass_tab_prefix(M, pass_count(M, 16), 16) : 0) + pass_tab_prefix(M, p, MAXR);
+}
+// complex64 entries of the whole twiddle allocation
+__host__ __device__ constexpr int tw_alloc_len(int M) {
+    return M + pass_tab_prefix(M, pass_count(M, 16), 16) + pass_tab_prefix(M, pass_count(M, 8), 8);
+}
+
 // ---- barriers ----------------------------------------------------------------
 
 // Barrier between the passes of a line: the whole block (__syncthreads), or a
@@ -275,7 +305,10 @@ __device__ __forceinline__ void apply_twiddles(const float2* __restrict__ tw, in
     }
 }
 
-template <int M, int R, int NS, int TPL, bool INV, class Src, class Dst, class SYNC>
+// TWT: the twiddles of a pass with NS > 1 come from the pass's own table
+// (TB: its offset in tw), one coalesced load each, instead of from the base
+// table with products
+template <int M, int R, int NS, int TPL, bool INV, bool TWT, int TB, class Src, class Dst, class SYNC>
 __device__ __forceinline__ void stockham_pass(int t, const Src& src, const Dst& dst,
                                               const float2* __restrict__ tw, bool sync_mid, const SYNC& sync) {
     constexpr int NB = M / R;
@@ -305,8 +338,17 @@ __device__ __forceinline__ void stockham_pass(int t, const Src& src, const Dst& 
         if ((NB % TPL) == 0 || j < NB) {
             const int k = (NS == 1) ? 0 : (j % NS);
             if (NS > 1) {
-                constexpr int STEP = M / (NS * R);
-                apply_twiddles<R, INV>(tw, k * STEP, a[it]);
+                if constexpr (TWT) {
+                    const float2* tp = tw + TB + k;
+#pragma unroll
+                    for (int s = 1; s < R; ++s) {
+                        const float2 w = __ldg(tp + (s - 1) * NS);
+                        a[it][s] = INV ? cmulc(a[it][s], w) : cmul(a[it][s], w);
+                    }
+                } else {
+                    constexpr int STEP = M / (NS * R);
+                    apply_twiddles<R, INV>(tw, k * STEP, a[it]);
+                }
             }
             Dft<R, INV>::run(a[it]);
             const int base = (j / NS) * NS * R + k;
@@ -331,34 +373,37 @@ __device__ __forceinline__ void stockham_pass(int t, const Src& src, const Dst& 
 // Run passes PIDX.. of the length-M transform.  Pass 0 reads `src`, the last
 // pass writes `dst`; the others go through the shared-memory line `sm`.
 // Every thread that `sync` covers must call this (it contains barriers).
-template <int M, int TPL, bool INV, int MAXR, int PIDX, int NS, class Src, class Dst, class SYNC>
+template <int M, int TPL, bool INV, int MAXR, int PIDX, int NS, bool TWT, class Src, class Dst, class SYNC>
 __device__ __forceinline__ void fft_run(int t, const Src& src, const Dst& dst, const SmemLine& sm,
                                         const float2* __restrict__ tw, const SYNC& sync) {
     constexpr int R = radix_of(M, PIDX, MAXR);
     constexpr bool LAST = (NS * R == M);
+    constexpr int TB = pass_tab_base(M, MAXR, PIDX);
     if constexpr (PIDX == 0) {
         if constexpr (LAST) {
-            stockham_pass<M, R, NS, TPL, INV>(t, src, dst, tw, Src::kSmem && Dst::kSmem, sync);
+            stockham_pass<M, R, NS, TPL, INV, TWT, TB>(t, src, dst, tw, Src::kSmem && Dst::kSmem, sync);
         } else {
-            stockham_pass<M, R, NS, TPL, INV>(t, src, sm, tw, Src::kSmem, sync);
+            stockham_pass<M, R, NS, TPL, INV, TWT, TB>(t, src, sm, tw, Src::kSmem, sync);
             sync();
-            fft_run<M, TPL, INV, MAXR, PIDX + 1, NS * R>(t, src, dst, sm, tw, sync);
+            fft_run<M, TPL, INV, MAXR, PIDX + 1, NS * R, TWT>(t, src, dst, sm, tw, sync);
         }
     } else {
         if constexpr (LAST) {
-            stockham_pass<M, R, NS, TPL, INV>(t, sm, dst, tw, Dst::kSmem, sync);
+            stockham_pass<M, R, NS, TPL, INV, TWT, TB>(t, sm, dst, tw, Dst::kSmem, sync);
         } else {
-            stockham_pass<M, R, NS, TPL, INV>(t, sm, sm, tw, true, sync);
+            stockham_pass<M, R, NS, TPL, INV, TWT, TB>(t, sm, sm, tw, true, sync);
             sync();
-            fft_run<M, TPL, INV, MAXR, PIDX + 1, NS * R>(t, src, dst, sm, tw, sync);
+            fft_run<M, TPL, INV, MAXR, PIDX + 1, NS * R, TWT>(t, src, dst, sm, tw, sync);
         }
     }
 }
 
-template <int M, int TPL, bool INV, int MAXR = 16, class Src, class Dst, class SYNC = BlockSync>
+// TWT: twiddles from the per-pass tables (one coalesced load each) instead of
+// four base-table loads and products per butterfly
+template <int M, int TPL, bool INV, int MAXR = 16, bool TWT = false, class Src, class Dst, class SYNC = BlockSync>
 __device__ __forceinline__ void fft_line(int t, const Src& src, const Dst& dst, const SmemLine& sm,
                                          const float2* __restrict__ tw, const SYNC& sync = SYNC()) {
-    fft_run<M, TPL, INV, MAXR, 0, 1>(t, src, dst, sm, tw, sync);
+    fft_run<M, TPL, INV, MAXR, 0, 1, TWT>(t, src, dst, sm, tw, sync);
 }
 
 // The transform of a line whose values thread t already holds in registers,
@@ -368,7 +413,7 @@ __device__ __forceinline__ void fft_line(int t, const Src& src, const Dst& dst, 
 // directly and only its outputs go to the shared-memory line `sm`; the later
 // passes are those of fft_line.  Call with every thread of the block; `sm`
 // must be free for writing (the caller's barrier).
-template <int M, int TPL, bool INV, int MAXR = 16, class Dst, class SYNC = BlockSync>
+template <int M, int TPL, bool INV, int MAXR = 16, class Dst, class SYNC = BlockSync, bool TWT = false>
 __device__ __forceinline__ void fft_line_regs(int t, float2 (&x)[M / TPL], const Dst& dst, const SmemLine& sm,
                                               const float2* __restrict__ tw, const SYNC& sync = SYNC()) {
     constexpr int R = radix_of(M, 0, MAXR);
@@ -402,7 +447,7 @@ __device__ __forceinline__ void fft_line_regs(int t, float2 (&x)[M / TPL], const
     }
     if constexpr (R < M) {
         sync();
-        fft_run<M, TPL, INV, MAXR, 1, R>(t, sm, dst, sm, tw, sync);
+        fft_run<M, TPL, INV, MAXR, 1, R, TWT>(t, sm, dst, sm, tw, sync);
     }
 }
 

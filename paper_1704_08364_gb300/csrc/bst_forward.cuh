@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(TPL * LPC, (TPL * LPC <= 1024) ? 1024 / (TPL *
     extern __shared__ float2 smem[];
     const int pl = blockIdx.y;
     const int sa = 2 * (pair0 + pl), sb = sa + 1;
-    ray_unit<M, TPL, LPC, MAXR, NC, BlockSync, ILV>(smem, blockIdx.x * LPC, V, N, sino + (size_t)sa * V * N,
+    ray_unit<M, TPL, LPC, MAXR, NC, BlockSync, ILV, true>(smem, blockIdx.x * LPC, V, N, sino + (size_t)sa * V * N,
                                                     sb < slices ? sino + (size_t)sb * V * N : nullptr, mode, g,
                                                     two_alpha, Z + (size_t)pl * V * M, tw);
 }

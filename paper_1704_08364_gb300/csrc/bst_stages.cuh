@@ -391,10 +391,10 @@ template <int M, bool ILV> __host__ __device__ constexpr int ray_line_stride() {
 
 // P2 + P3 + P4 for lines j0 .. j0 + LPC - 1 of one slice pair (TPL * LPC
 // threads; tid the thread's index among them, -1: threadIdx.x; `sync` the
-// barrier that covers them).  ILV: thread tid works on line tid % LPC, so a
+// barrier that covers them; TWT: twiddles from the per-pass tables).  ILV: thread tid works on line tid % LPC, so a
 // warp holds the same bins of LPC consecutive angle rows, whose slots the
 // paired layout keeps in the same 128-byte lines.
-template <int M, int TPL, int LPC, int MAXR, int NC = 0, class SYNC = BlockSync, bool ILV = false>
+template <int M, int TPL, int LPC, int MAXR, int NC = 0, class SYNC = BlockSync, bool ILV = false, bool TWT = false>
 __device__ __forceinline__ void ray_unit(float2* smem, int j0, int V, int N, const float* __restrict__ ya,
                                          const float* __restrict__ yb, int mode, const float* __restrict__ g,
                                          float two_alpha, float2* __restrict__ Zp, const float2* __restrict__ tw,
@@ -407,7 +407,7 @@ __device__ __forceinline__ void ray_unit(float2* smem, int j0, int V, int N, con
     RaySrc<NC> src{ya + (size_t)jj * N, yb ? yb + (size_t)jj * N : nullptr, N, M, live};
     SpecDst dst{Zp, jj, V, g, M, mode, two_alpha, live};
     SmemLine sm{smem + line * ray_line_stride<M, ILV>()};
-    fft_line<M, TPL, false, MAXR>(t, src, dst, sm, tw, sync);
+    fft_line<M, TPL, false, MAXR, TWT>(t, src, dst, sm, tw, sync);
 }
 
 // P0 + P5 + column P6 for column pairs q0 .. q0 + CPC - 1 (blockDim = TPL * CPC):
@@ -786,7 +786,7 @@ __device__ __forceinline__ void grid_unit_xchg(float2* smem, int q, int V, int N
 // RPT b + RPT - 1.  RPT = 4 reads T in whole 32-byte groups of four rows; a
 // worker too small for four lines takes RPT = 2.  va, vb: the [N][N] images
 // of slices a and b (vb may be null)
-template <int M, int TPL, int TPC, int MAXR, int NC = 0, class SYNC = BlockSync, int RPT = 4>
+template <int M, int TPL, int TPC, int MAXR, int NC = 0, class SYNC = BlockSync, int RPT = 4, bool TWT = false>
 __device__ __forceinline__ void row_unit(float2* smem, int rb0, int N, const float2* __restrict__ Tp,
                                          float* __restrict__ va, float* __restrict__ vb, float scale,
                                          const float2* __restrict__ tw, const float* __restrict__ dk = nullptr,
@@ -803,7 +803,7 @@ __device__ __forceinline__ void row_unit(float2* smem, int rb0, int N, const flo
     VolDst<NC> dst{va + (size_t)rr * N, vb ? vb + (size_t)rr * N : nullptr, N, M,
                dk ? scale * __ldg(dk + rr) : scale, live, dk};
     SmemLine sm{smem + (tile * RPT + line) * row_line_stride<M>()};
-    fft_line<M, TPL, true, MAXR>(t, src, dst, sm, tw, sync);
+    fft_line<M, TPL, true, MAXR, TWT>(t, src, dst, sm, tw, sync);
 }
 
 }  // namespace bst
