@@ -11,8 +11,8 @@
 #include <new>
 #include <vector>
 
-#include "bst_fft.cuh"
 #include "bst_internal.h"
+#include "bst_twiddle.h"
 
 namespace {
 
@@ -160,19 +160,7 @@ bst_status_t bst_plan_create(bst_plan_t* out, int rays, int angles, const float*
     const int V = angles;
 
     // twiddles: the base table, then each radix schedule's per-pass tables
-    // (entry (s - 1) NS + k of pass p = tw[k s M / (NS R)], see bst_fft.cuh)
-    std::vector<float2> tw(bst::tw_alloc_len(M));
-    for (int m = 0; m < M; ++m) {
-        const double a = -2.0 * M_PI * (double)m / (double)M;
-        tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
-    for (int maxr : {16, 8})
-        for (int pp = 1; pp < bst::pass_count(M, maxr); ++pp) {
-            const int R = bst::radix_of(M, pp, maxr), NS = bst::pass_ns(M, pp, maxr);
-            const int base = bst::pass_tab_base(M, maxr, pp), step = M / (NS * R);
-            for (int s = 1; s < R; ++s)
-                for (int k = 0; k < NS; ++k) tw[base + (s - 1) * NS + k] = tw[k * s * step];
-        }
+    const std::vector<float2> tw = bst::make_twiddles(M);
     std::vector<double> ext(V + 2);
     ext[0] = th[V - 1] - M_PI;
     for (int j = 0; j < V; ++j) ext[j + 1] = th[j];

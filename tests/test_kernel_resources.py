@@ -67,3 +67,20 @@ def test_paired_layout_slot_map_is_a_bijection(tmp_path):
     assert r.returncode == 0, r.stdout + r.stderr
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert out.returncode == 0 and out.stdout.strip() == "OK", out.stdout + out.stderr
+
+
+def test_twiddle_tables_tile_the_allocation_with_exact_values(tmp_path):
+    """The per-pass twiddle tables that the ray kernel reads (bst_twiddle.h,
+    pass_tab_base in bst_fft.cuh) cover the plan's twiddle allocation exactly
+    once for every FFT length and both radix schedules, and hold
+    exp(-2 pi i k s / (NS R)) to float rounding."""
+    nvcc = NVCC if os.path.exists(NVCC) else shutil.which("nvcc")
+    if not nvcc:
+        pytest.skip("nvcc not available")
+    exe = tmp_path / "twiddle_check"
+    r = subprocess.run([nvcc, "-std=c++17", "-O2", "-I", os.path.join(ROOT, "paper_1704_08364_gb300", "csrc"),
+                        "-I", os.path.join(ROOT, "include"), "-x", "cu", os.path.join(ROOT, "tests", "twiddle_check.cu"),
+                        "-o", str(exe)], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and out.stdout.strip() == "OK", out.stdout + out.stderr
