@@ -69,3 +69,32 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         _lib.load(str(tmp_path / "libbst.so"))
+
+
+def test_forward_config_struct_matches_the_binding(tmp_path):
+    """bst_fwd_config_t as the C compiler lays it out (size, and the offset of
+    each field in header order) equals the binding's ctypes structure, so a
+    field added to one side without the other fails here, not in a GPU call."""
+    import shutil
+    import subprocess
+    from paper_1704_08364_gb300 import _lib
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    txt = open(os.path.join(ROOT, "include", "bst.h")).read()
+    body = re.search(r"typedef struct \{(.*?)\} bst_fwd_config_t;", txt, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\bint\s+(\w+)\s*;", body)
+    assert fields == [f for f, _ in _lib.FwdConfig._fields_]
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n"
+                   "typedef struct {" + body + "} cfg_t;\n"
+                   "int main(void) { printf(\"%zu\", sizeof(cfg_t));"
+                   + "".join(f' printf(" %zu", offsetof(cfg_t, {f}));' for f in fields)
+                   + " printf(\"\\n\"); return 0; }\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", str(src), "-o", str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, timeout=60).stdout.split()]
+    want = [ctypes.sizeof(_lib.FwdConfig)] + [getattr(_lib.FwdConfig, f).offset for f in fields]
+    assert got == want

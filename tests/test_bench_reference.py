@@ -35,3 +35,22 @@ def test_reference_line_keeps_the_contract():
 
 def test_reference_ranks_other_than_zero_do_no_work():
     assert _run({"WORLD_SIZE": "2", "RANK": "1"}, "--rays", "64", "--steps", "1", "--warmup", "1") == []
+
+
+def test_stored_traffic_applies_only_to_its_device_code_and_shape(monkeypatch):
+    """The ncu traffic record is used only while the kernels' device code hashes
+    to the record's value and the benchmark runs the captured launch shape;
+    any other shape field (layout, chunk, block order, radix, gather form),
+    geometry or device code gives no traffic figure."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = bench.CAPTURED_TRAFFIC[0]
+    monkeypatch.setattr(bench, "device_code_sha", lambda: rec["sha"])
+    shape = dict(rec["shape"], max_lanes=2)
+    assert bench.captured_traffic("k_grid_col", rec["rays"], rec["pad"], shape) == rec["bytes"]["k_grid_col"]
+    for k, other in (("layout", "packed"), ("chunk_pairs", 4), ("pair_fast", 0), ("max_radix", 8), ("grid_xchg", 0)):
+        if shape[k] != other:
+            assert bench.captured_traffic("k_grid_col", rec["rays"], rec["pad"], dict(shape, **{k: other})) is None, k
+    assert bench.captured_traffic("k_grid_col", rec["rays"] // 2, rec["pad"], shape) is None
+    monkeypatch.setattr(bench, "device_code_sha", lambda: "0" * 64)
+    assert bench.captured_traffic("k_grid_col", rec["rays"], rec["pad"], shape) is None
